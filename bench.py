@@ -1,0 +1,418 @@
+"""Benchmark of the randomized bilinear computation on GB300.
+
+Workload (one "step"): the at-scale fp32 sweep of exact and approximate formulas --
+randomized Strassen N = 8192 with L = 1..4, randomized Laderman N = 6561 with L = 1..3,
+and a perturbed Strassen (Section 3.1 recipe, std 1e-3) N = 4096 with L = 1..3 -- ten
+rbc_matmul calls on fp32 I/O with A, B i.i.d. N(0,1) (seeded), per-node draws.
+
+Metric: effective TFLOP/s = sum of 2 N^3 over the step / step time (device time, CUDA
+events, inputs resident in HBM).  Every operand is larger than L2 or is followed by
+workspace writes larger than L2 before its next use.  `e2e` times the same calls with the
+host-to-device copies of A, B and the device-to-host copy of C inside the timed region.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload.  Multi-GPU: the path does not shard (no collectives): N replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "effective TFLOP/s (2n³/t) + rel. Frobenius error vs FP64 oracle; served p50/p99"
+WORKLOAD = "rbc-fp32-sweep: strassen n=8192 L=1..4, laderman n=6561 L=1..3, noisy-strassen(std 1e-3) n=4096 L=1..3"
+CASES = [("strassen", 8192, L) for L in (1, 2, 3, 4)] + \
+        [("laderman", 6561, L) for L in (1, 2, 3)] + \
+        [("noisy-strassen", 4096, L) for L in (1, 2, 3)]
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x fp32 lanes x 2 flop x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--leaf", default="f32")
+    ap.add_argument("--cases", default="all", help="'all' or comma list of indices into the sweep")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def case_flops(n, L, R, n0):
+    m = n // n0**L
+    return 2.0 * n**3, 2.0 * R**L * m**3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1905_07439_gb300 as rbc
+    from rbc_inputs import formula_by_name
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    leaf = rbc.LEAF_NAMES[args.leaf]
+    sel = list(range(len(CASES))) if args.cases == "all" else [int(x) for x in args.cases.split(",")]
+    cases = [CASES[i] for i in sel]
+
+    # Inputs: per distinct N one seeded N(0,1) pair, resident on the device, plus pinned host copies.
+    gen = torch.Generator(device="cpu")
+    inputs = {}
+    for _, n, _ in cases:
+        if n in inputs:
+            continue
+        gen.manual_seed(1000 + n)
+        A = torch.randn((n, n), generator=gen, dtype=torch.float32)
+        B = torch.randn((n, n), generator=gen, dtype=torch.float32)
+        inputs[n] = {"hA": A.pin_memory(), "hB": B.pin_memory(), "A": A.to(dev), "B": B.to(dev),
+                     "C": torch.empty((n, n), dtype=torch.float32, device=dev),
+                     "hC": torch.empty((n, n), dtype=torch.float32).pin_memory()}
+    plans = []
+    for name, n, L in cases:
+        U, V, W = formula_by_name(name, seed=7)
+        plans.append(rbc.Plan(U, V, W, levels=L, seed=2024 + L))
+    ws_bytes = max(p.workspace_size(n, rbc.IO_F32, leaf) for p, (_, n, _) in zip(plans, cases))
+    if ws_bytes == 0:
+        raise RuntimeError("invalid leaf mode for this workload")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def new_events():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for e in evs:
+            e.record(stream)   # materialize the CUDA event before handing it to the library
+        return evs
+
+    def step(events=None, counts=None):
+        for i, (plan, (name, n, L)) in enumerate(zip(plans, cases)):
+            x = inputs[n]
+            o = rbc.rbc.rbc_matmul_opts(0)
+            if events is not None:
+                for j, e in enumerate(events[i]):
+                    o.events[j] = e.cuda_event
+            import ctypes as C
+            rbc.rbc.check(rbc.lib().rbc_matmul_ex(
+                plan.handle, x["A"].data_ptr(), x["B"].data_ptr(), x["C"].data_ptr(), n, n, n, n,
+                rbc.IO_F32, leaf, ws.data_ptr(), ws.numel(), C.c_void_p(stream.cuda_stream), C.byref(o)),
+                "rbc_matmul_ex")
+            if counts is not None:
+                counts.append(o.launches)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ev_sets = [[new_events() for _ in cases] for _ in range(args.steps)]
+    counts = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t0.record(stream)
+        for s in range(args.steps):
+            step(ev_sets[s], counts)
+        t1.record(stream)
+        barrier()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    eff_flops = sum(case_flops(n, L, formula_by_name(nm, 7)[0].shape[2], formula_by_name(nm, 7)[0].shape[0])[0]
+                    for nm, n, L in cases)
+    value = world * eff_flops / (ms_step * 1e-3) / 1e12
+
+    # Leaf-product kernel (with fused decode): the dominant kernel.
+    leaf_ms, leaf_flops, enc_ms, enc_bytes = 0.0, 0.0, 0.0, 0.0
+    per_case = []
+    es_leaf = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2}[args.leaf]
+    split = 3 if args.leaf.startswith("3x") else 1
+    for i, (nm, n, L) in enumerate(cases):
+        U = formula_by_name(nm, 7)[0]
+        R, n0 = U.shape[2], U.shape[0]
+        m = n // n0**L
+        g = statistics.mean(ev_sets[s][i][1].elapsed_time(ev_sets[s][i][2]) for s in range(args.steps))
+        e = statistics.mean(ev_sets[s][i][0].elapsed_time(ev_sets[s][i][1]) for s in range(args.steps))
+        tot = statistics.mean(ev_sets[s][i][0].elapsed_time(ev_sets[s][i][3]) for s in range(args.steps))
+        lf = split * 2.0 * R**L * m**3
+        leaf_ms += g
+        leaf_flops += lf
+        # algorithmic encode bytes: read A, B once, write the leaf operands once
+        eb = 2 * 4 * n * n + 2 * es_leaf * split * R**L * m * m
+        enc_ms += e
+        enc_bytes += eb
+        per_case.append({"formula": nm, "n": n, "L": L, "ms": round(tot, 3),
+                         "eff_tflops": round(2.0 * n**3 / tot / 1e9, 2),
+                         "leaf_ms": round(g, 3), "leaf_tflops": round(lf / g / 1e9, 2),
+                         "encode_ms": round(e, 3), "encode_gbs": round(eb / e / 1e6, 1)})
+    pk, pk_kind = peaks()
+    if args.leaf in ("f32",):
+        bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
+        peak_note = "fp32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"
+    else:
+        ratio = 0.5 if args.leaf in ("tf32", "3xtf32") else 1.0
+        bound, unit = "tensor", "TFLOP/s"
+        peak = pk["bf16_tflops_sustained"] * ratio
+        peak_note = f"{pk_kind} bf16 sustained x {ratio} (nominal {args.leaf}/bf16 ratio)"
+    achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
+    roof = {"kernel": "leaf products + fused decode", "bound": bound, "achieved": round(achieved, 2),
+            "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": peak_note,
+            "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
+                       "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}}
+    launches_per_step = sum(counts) // max(1, args.steps)
+
+    # End to end through the public API: H2D of A and B, the call, D2H of C, per case.
+    e2e = None
+    if not args.no_e2e:
+        def e2e_step():
+            for plan, (nm, n, L) in zip(plans, cases):
+                x = inputs[n]
+                x["A"].copy_(x["hA"], non_blocking=True)
+                x["B"].copy_(x["hB"], non_blocking=True)
+                rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws)
+                x["hC"].copy_(x["C"], non_blocking=True)
+        e2e_step()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        a1.record(stream)
+        barrier()
+        e_ms = a0.elapsed_time(a1) / args.steps
+        e2e = {"value": round(world * eff_flops / (e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+               "ms_per_step": round(e_ms, 3),
+               "h2d_bytes_per_step": sum(2 * 4 * n * n for _, n, _ in cases),
+               "d2h_bytes_per_step": sum(4 * n * n for _, n, _ in cases)}
+
+    # Error against our own fp64 classical product (L = 0, fp64 SIMT GEMM), per distinct input.
+    errors = []
+    with torch.no_grad():
+        truths = {}
+        one = rbc.Plan(*formula_by_name("strassen"), levels=0)
+        for _, n, _ in cases:
+            if n in truths:
+                continue
+            A64 = inputs[n]["A"].double()
+            B64 = inputs[n]["B"].double()
+            truths[n] = rbc.matmul(one, A64, B64, leaf=rbc.LEAF_F64)
+            del A64, B64
+        for plan, (nm, n, L) in zip(plans, cases):
+            x = inputs[n]
+            rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws)
+            nr = rbc.norms(x["C"], truths[n]).cpu().numpy()
+            errors.append({"formula": nm, "n": n, "L": L, "rel_fro_vs_fp64_ab": float(np.sqrt(nr[0] / nr[1]))})
+        torch.cuda.synchronize(dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(budget_s=15.0, gpu_check=(plans, cases, inputs, ws, leaf))
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.leaf == "f32" else f"f32 io, {args.leaf} leaves",
+        "data": "synthetic (seeded N(0,1); perturbed Strassen per Section 3.1)",
+        "config": {"workload": WORKLOAD, "io": "f32", "leaf": args.leaf, "draws": "per-node",
+                   "cases": len(cases), "parallelism": f"replicas x{world}",
+                   "l2": "inputs and per-case workspaces larger than L2 (129 MB)"},
+        "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
+        "e2e": e2e, "cpu_baseline": cpu, "cases": per_case, "errors": errors,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_cases(budget_s):
+    """Cases for the bounded CPU sample: cheapest first, until the budget is spent."""
+    order = [i for i, c in sorted(enumerate(CASES), key=lambda ic: ic[1][1] ** 3 * 0.9 ** ic[1][2])]
+    return order
+
+
+def cpu_baseline(budget_s=15.0, gpu_check=None):
+    """The FP64 oracle on the host cores, bounded sample of the workload (cheapest cases
+    first until about `budget_s` seconds of CPU work)."""
+    import numpy as np
+
+    from oracle import rbc_oracle as o
+    from rbc_inputs import formula_by_name
+
+    done, flops, secs, errs = [], 0.0, 0.0, []
+    rng_cache = {}
+    for i in _oracle_cases(budget_s):
+        nm, n, L = CASES[i]
+        if secs > budget_s:
+            break
+        if gpu_check is not None and n not in gpu_check[2]:
+            continue
+        if n not in rng_cache:
+            if gpu_check is not None:
+                x = gpu_check[2][n]
+                rng_cache[n] = (x["hA"].numpy().astype(np.float64), x["hB"].numpy().astype(np.float64))
+            else:
+                g = np.random.Generator(np.random.PCG64(1000 + n))
+                rng_cache[n] = (g.standard_normal((n, n)).astype(np.float32).astype(np.float64),
+                                g.standard_normal((n, n)).astype(np.float32).astype(np.float64))
+        A, B = rng_cache[n]
+        U, V, W = formula_by_name(nm, seed=7)
+        t = time.perf_counter()
+        C = o.rbc(A, B, o.Plan(U, V, W, levels=L, seed=2024 + L))
+        dt = time.perf_counter() - t
+        secs += dt
+        flops += 2.0 * n**3
+        done.append(f"{nm} n={n} L={L}")
+        if gpu_check is not None:
+            plans, cases, inputs, ws, leaf = gpu_check
+            import torch
+
+            import paper_1905_07439_gb300 as rbc
+            j = cases.index((nm, n, L)) if (nm, n, L) in cases else None
+            if j is not None:
+                x = inputs[n]
+                rbc.matmul(plans[j], x["A"], x["B"], x["C"], leaf=leaf, workspace=ws)
+                Cg = x["C"].double().cpu().numpy()
+                errs.append({"case": f"{nm} n={n} L={L}",
+                             "rel_fro_vs_oracle": float(np.linalg.norm(Cg - C) / np.linalg.norm(C)),
+                             "normwise_vs_oracle": float(np.linalg.norm(Cg - C) / (np.linalg.norm(A) * np.linalg.norm(B)))})
+        del C
+    return {"value": round(flops / secs / 1e12, 5), "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": "; ".join(done) + f" ({secs:.1f} s, numpy fp64)",
+            "parity": errs}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per = []
+    for _ in range(args.warmup):
+        pass
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline(budget_s=max(2.0, 20.0 / max(1, args.steps)))
+        per.append(res["value"])
+    dt = time.perf_counter() - t0
+    value = statistics.mean(per)
+    line = {"metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded N(0,1))", "impl": "reference",
+            "config": {"workload": WORKLOAD, "io": "f64 oracle"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "TFLOP/s", "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

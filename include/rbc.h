@@ -1,0 +1,194 @@
+/*
+ * rbc.h -- C ABI of the randomized bilinear computation (RBC) library for GB300 (sm_103a).
+ *
+ * The library evaluates C = F^(L)(A, B), the recursive randomized bilinear computation of
+ * Malik & Becker, "Randomization of approximate bilinear computation for matrix
+ * multiplication" (arXiv 1905.07439), Section 2.1.1, Eq. recursive-random-formula:
+ * at every node of an L-level recursion the n0 x n0 block indices of a bilinear formula
+ * (U, V, W) (Section 1, Eq. (1)) are randomized by signed permutations M_i = P_i S_i
+ * (Section 2.1), folded into coefficient tables u^, v^, w^ (Prop. 10, Eq. randomized-algorithm):
+ *
+ *     u^_klr  = u_{pi1(k) pi2(l) r} s1(k) s2(l)
+ *     v^_k'l'r = v_{pi2(k') pi3(l') r} s2(k') s3(l')
+ *     w^_ijr  = (1 - kappa)^{-1} s1(i) s3(j) w_{pi1(i) pi3(j) r}
+ *
+ * and the node computes S_r = sum u^_klr A_kl, T_r = sum v^_k'l'r B_k'l' (encode),
+ * M_r = F^(q-1)(S_r, T_r) (the leaves, q = 0, are standard products) and
+ * C_ij = sum_r w^_ijr M_r (decode).  kappa is Eq. epsilon-def.
+ *
+ * Conventions for every call:
+ *   - Matrices are row-major with a leading dimension (ld, in elements, >= N).
+ *   - Tensors U, V, W are float64 arrays of n0*n0*R entries, entry (k, l, r) at
+ *     index (k*n0 + l)*R + r (0-based), as in Eq. (1).
+ *   - Device pointers are caller-owned CUDA global memory on the current device;
+ *     host pointers are caller-owned host memory.  The library keeps no pointer
+ *     past the return of a call.
+ *   - Every call returns an rbc_status and never aborts the process; the text of the
+ *     last error of the calling thread is available from rbc_last_error().
+ *   - Device work is enqueued on the given stream (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream) and is asynchronous with respect to the host.
+ */
+#ifndef RBC_H_
+#define RBC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbc_plan_s* rbc_plan_t;
+
+typedef enum {
+  RBC_OK = 0,
+  RBC_EINVAL = 1,       /* invalid argument (shape, size, enum, null pointer)           */
+  RBC_ENOMEM = 2,       /* workspace too small or a host allocation failed              */
+  RBC_ECUDA = 3,        /* a CUDA runtime call failed (no device, launch error, ...)    */
+  RBC_ETIMEOUT = 4,     /* a bounded device-side wait expired                           */
+  RBC_EBUSY = 5,        /* queue full / request still in flight                         */
+  RBC_EKAPPA = 6,       /* kappa == 1, the randomized formula is undefined (Def. RandABC) */
+  RBC_EUNSUPPORTED = 7  /* valid but not implemented combination (dtype pair, tree size) */
+} rbc_status;
+
+/* Element type of A, B and C. */
+typedef enum { RBC_IO_F64 = 0, RBC_IO_F32 = 1 } rbc_io_dtype;
+
+/* Arithmetic of the leaf products F^(0) (Section 2.1.1).  Encode and decode run in the
+ * I/O type; leaves accumulate in fp32 (fp64 for RBC_LEAF_F64).  The split modes store
+ * x = hi + lo with hi = round(x), lo = round(x - hi) and compute hi*hi' + hi*lo' + lo*hi'. */
+typedef enum {
+  RBC_LEAF_F64 = 0,    /* fp64 FMA (SIMT); I/O must be F64                         */
+  RBC_LEAF_F32 = 1,    /* fp32 FMA (SIMT)                                          */
+  RBC_LEAF_TF32 = 2,   /* tcgen05 kind::tf32, fp32 accumulate in TMEM               */
+  RBC_LEAF_BF16 = 3,   /* tcgen05 kind::f16 with bf16 operands                      */
+  RBC_LEAF_F16 = 4,    /* tcgen05 kind::f16 with fp16 operands                      */
+  RBC_LEAF_3XBF16 = 5, /* three bf16 tcgen05 products (split compensated)          */
+  RBC_LEAF_3XTF32 = 6  /* three tf32 tcgen05 products (split compensated)          */
+} rbc_leaf_dtype;
+
+/* Which parts of the signed permutations are drawn (Section 3.2: fully randomized,
+ * random sign, random permutation; deterministic F^(Q) has s = 1, pi = id). */
+typedef enum { RBC_RAND_FULL = 0, RBC_RAND_SIGN = 1, RBC_RAND_PERM = 2, RBC_RAND_NONE = 3 } rbc_rand_mode;
+
+/* One independent draw set per recursion node, or one per recursion level
+ * (the literal definition of Section 2.1.1). */
+typedef enum { RBC_DRAW_PER_NODE = 0, RBC_DRAW_PER_LEVEL = 1 } rbc_draw_scope;
+
+typedef struct {
+  const double* U;   /* host, n0*n0*R, copied by the plan                             */
+  const double* V;
+  const double* W;
+  int R;             /* number of products, 1 <= R <= 4096; the kernels need
+                        n0*n0*R <= 256 and, per launch, at most 1024 draw sets        */
+  int n0;            /* block dimension of the formula (the paper's n), 2 <= n0 <= 4  */
+  int levels;        /* recursion levels L (the paper's Q), 0 <= L <= 8               */
+  uint64_t seed;     /* seed of the counter-based draws                               */
+  int rand_mode;     /* rbc_rand_mode                                                 */
+  int draw_scope;    /* rbc_draw_scope                                                */
+  int rescale_kappa; /* -1: rescale by (1-kappa)^-1 iff randomized; 0: never; 1: always */
+} rbc_plan_desc;
+
+typedef struct {
+  int R, n0, levels, rand_mode, draw_scope;
+  int64_t draw_count;  /* draw sets held: sum_{d<L} R^d (per node) or L (per level)   */
+  int64_t leaf_count;  /* R^L leaf products                                           */
+  double kappa;        /* Eq. epsilon-def                                             */
+  double tau;          /* ||Y - X||, Def. ABC                                          */
+  double gamma;        /* Eq. square-root-of-sum                                      */
+  double scale;        /* (1 - kappa)^{-1} if rescaled, else 1                         */
+  uint64_t seed;
+} rbc_plan_info;
+
+/* Draws (Section 2.1).  Counter-based: draw set `key` uses the six words
+ *   w_c = mix64(seed + 0x9E3779B97F4A7C15 * (1 + 8*key + c)),  c = 0..5,
+ * mix64 being the SplitMix64 output function.  pi_{c+1} (c = 0,1,2) is Fisher-Yates
+ * from i = n0-1 down to 1 swapping p[i] and p[j], j = floor(mix64(w_c + i) * (i+1) / 2^64),
+ * pi(j) = p[j]; s_{c-2}(j) = -1 iff bit j of w_c (c = 3,4,5) is set.  key is the node id in
+ * heap order (root 0, child r of node p is p*R + r + 1) for per-node scope, or the depth
+ * (root 0) for per-level scope. */
+
+/* Create a plan with full randomization, per-node draws, default rescaling.
+ * Errors: RBC_EINVAL (null pointer, R/n0/levels out of range), RBC_EKAPPA (kappa == 1),
+ * RBC_ENOMEM.  Host-only: touches no device.  *out is owned by the caller and released
+ * with rbc_plan_destroy. */
+rbc_status rbc_plan_create(const double* U, const double* V, const double* W, int R, int n0,
+                           int levels, uint64_t seed, rbc_plan_t* out);
+
+/* Same with every option of rbc_plan_desc (Section 3.2 variants, draw scope, rescaling). */
+rbc_status rbc_plan_create_ex(const rbc_plan_desc* desc, rbc_plan_t* out);
+
+/* Release a plan (NULL is ignored).  No device work may still use it. */
+void rbc_plan_destroy(rbc_plan_t plan);
+
+/* Constants of the plan (Eq. epsilon-def, Def. ABC, Eq. square-root-of-sum). */
+rbc_status rbc_plan_query(rbc_plan_t plan, rbc_plan_info* info);
+
+/* Export draw sets [first, first+count) for bit-exact checks: perms[(t*3 + c)*n0 + j] =
+ * pi_{c+1}(j), signs[(t*3 + c)*n0 + j] = s_{c+1}(j) in {-1, +1}.  Host buffers of
+ * count*3*n0 bytes each.  RBC_EINVAL if the range exceeds draw_count. */
+rbc_status rbc_plan_draws(rbc_plan_t plan, int64_t first, int64_t count, int8_t* perms,
+                          int8_t* signs);
+
+/* Expanded tables u^, v^, w^ (Prop. 10) of draw set `key`, each n0*n0*R float64 in the
+ * layout of U.  w^ includes the plan's scale. */
+rbc_status rbc_plan_tables(rbc_plan_t plan, int64_t key, double* Uhat, double* Vhat,
+                           double* What);
+
+/* Bytes of device workspace rbc_matmul needs for an N x N product with these types
+ * (0 when the combination is invalid; 256-byte aligned pointer required). */
+size_t rbc_workspace_size(rbc_plan_t plan, int64_t N, int io_dtype, int leaf_dtype);
+
+/* C = F^(L)(A, B) for N x N matrices, N a multiple of n0^L (pad first, Section 2.1.1).
+ * A, B: device, read only; C: device, overwritten (must not alias A or B).
+ * workspace: device scratch of at least rbc_workspace_size() bytes, contents undefined
+ * on return; two calls in flight at once need two workspaces.
+ * Errors: RBC_EINVAL (N, ld, dtype pair, alignment), RBC_ENOMEM (workspace too small),
+ * RBC_EUNSUPPORTED (tree deeper than the kernel tables hold), RBC_ECUDA (launch failure). */
+rbc_status rbc_matmul(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N,
+                      int64_t lda, int64_t ldb, int64_t ldc, int io_dtype, int leaf_dtype,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* Options of rbc_matmul_ex.  decode: 0 = fused into the leaf products when the kernel
+ * tables hold the whole tree, else level by level; 1 = fused (RBC_EUNSUPPORTED if the tree
+ * is too large); 2 = level by level (the leaf products are stored, then each level's
+ * C_ij = sum_r w^_ijr M_r runs as its own pass, r in order, so the result is bitwise
+ * reproducible).  The fused decode adds each leaf's contribution to C with atomic adds,
+ * so its summation order, and the last bits of C, may vary from call to call. */
+typedef struct {
+  int decode;
+  int reserved[7];
+  /* Optional timing hooks: CUDA events (cudaEvent_t as void*, NULL = skip) recorded on the
+   * call's stream at [0] the start, [1] the end of the encode, [2] the end of the leaf
+   * products (including a fused decode), [3] the end of the call. */
+  void* events[4];
+  /* Output: number of kernels the call launched (memsets not counted). */
+  int64_t launches;
+} rbc_matmul_opts;
+
+/* rbc_workspace_size / rbc_matmul with options (opts may be NULL = defaults; rbc_matmul_ex
+ * writes opts->launches). */
+size_t rbc_workspace_size_ex(rbc_plan_t plan, int64_t N, int io_dtype, int leaf_dtype,
+                             const rbc_matmul_opts* opts);
+rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N,
+                         int64_t lda, int64_t ldb, int64_t ldc, int io_dtype, int leaf_dtype,
+                         void* workspace, size_t workspace_bytes, void* stream,
+                         rbc_matmul_opts* opts);
+
+/* Frobenius reductions in fp64 (Section 3's relative errors): out[0] = sum (X - Y)^2,
+ * out[1] = sum Y^2 (Y == NULL: out[0] = sum X^2, out[1] = 0).  X, Y: device, rows x cols
+ * row-major with lds ldx, ldy, element types rbc_io_dtype.  out: device, 2 doubles.
+ * work: device scratch of rbc_norms_work_size() bytes.  Deterministic order. */
+rbc_status rbc_norms(const void* X, const void* Y, int64_t rows, int64_t cols, int64_t ldx,
+                     int64_t ldy, int x_dtype, int y_dtype, double* out, void* work,
+                     size_t work_bytes, void* stream);
+size_t rbc_norms_work_size(void);
+
+const char* rbc_status_string(rbc_status status);
+const char* rbc_last_error(void);
+int rbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBC_H_ */

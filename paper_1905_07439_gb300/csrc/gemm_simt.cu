@@ -1,0 +1,153 @@
+// Leaf products F^(0)(S, T) = S T (Section 2.1.1) on the CUDA cores, batched over all R^L
+// leaves, for the fp64 and fp32 leaf modes (the tensor cores have no fp32-input or fast
+// fp64 path).  Optional fused decode: the epilogue scatters the leaf's tile into every C
+// block (I, J) with coefficient prod_d w^(node_d)_{i_d j_d r_d} (Eq. recursive-random-formula
+// unrolled over the levels), by atomic adds into a zeroed C.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "decode_dest.cuh"
+#include "level_kernels.cuh"
+
+namespace rbc {
+
+namespace {
+
+template <typename T, int E>
+__device__ __forceinline__ void load_vec(T (&dst)[E], const T* src) {
+  if constexpr (E * sizeof(T) == 16) {
+    const int4 v = *reinterpret_cast<const int4*>(src);
+    memcpy(dst, &v, 16);
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) dst[e] = src[e];
+  }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    simt_gemm_kernel(const __grid_constant__ Tables<T> t, const SimtGemmArgs a) {
+  constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
+  constexpr int EA = BM * BK / NT, EB = BN * BK / NT;
+  static_assert(BK % EA == 0 && BK % EB == 0, "tile/thread mismatch");
+  constexpr int KA = BK / EA, KB = BK / EB;  // threads per tile row
+  __shared__ T As[2][BK][BM];
+  __shared__ T Bs[2][BK][BN];
+  __shared__ DestList<T> dl;
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int64_t row0 = (int64_t)blockIdx.y * BM, col0 = (int64_t)blockIdx.x * BN;
+  const int ar = tid / KA, ak = (tid % KA) * EA;
+  const int br = tid / KB, bk = (tid % KB) * EB;
+  const int nk = (int)(a.K / BK);
+
+  for (int64_t leaf = blockIdx.z; leaf < a.leaves; leaf += gridDim.z) {
+    const T* S = static_cast<const T*>(a.S) + leaf * a.strideS + (row0 + ar) * a.lds + ak;
+    const T* Tt = static_cast<const T*>(a.Tt) + leaf * a.strideT + (col0 + br) * a.ldt + bk;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
+
+    T ra[EA], rb[EB];
+    load_vec<T, EA>(ra, S);
+    load_vec<T, EB>(rb, Tt);
+    __syncthreads();  // previous leaf's readers are done with buffer 0
+#pragma unroll
+    for (int e = 0; e < EA; ++e) As[0][ak + e][ar] = ra[e];
+#pragma unroll
+    for (int e = 0; e < EB; ++e) Bs[0][bk + e][br] = rb[e];
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+      const int buf = kt & 1;
+      if (kt + 1 < nk) {
+        load_vec<T, EA>(ra, S + (int64_t)(kt + 1) * BK);
+        load_vec<T, EB>(rb, Tt + (int64_t)(kt + 1) * BK);
+      }
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) av[i] = As[buf][kk][ty + i * TY];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx + j * TX];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+      if (kt + 1 < nk) {
+#pragma unroll
+        for (int e = 0; e < EA; ++e) As[buf ^ 1][ak + e][ar] = ra[e];
+#pragma unroll
+        for (int e = 0; e < EB; ++e) Bs[buf ^ 1][bk + e][br] = rb[e];
+      }
+      __syncthreads();
+    }
+
+    if (a.mode == 0) {
+      T* M = static_cast<T*>(a.out) + leaf * a.strideO;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+          M[(row0 + ty + i * TY) * a.ldo + col0 + tx + j * TX] = acc[i][j];
+    } else if (a.mode == 2) {
+      T* C = static_cast<T*>(a.out);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const int64_t r = row0 + ty + i * TY, c = col0 + tx + j * TX;
+          if (r < a.m && c < a.m) C[r * a.ldo + c] = acc[i][j];
+        }
+    } else {
+      if (tid == 0) build_dest_list(t, leaf, dl);
+      __syncthreads();
+      T* C = static_cast<T*>(a.out);
+      for (int d = 0; d < dl.total; ++d) {
+        int64_t I, J;
+        const T coef = dest_at(dl, d, t.n0, t.L, &I, &J);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const int64_t r = row0 + ty + i * TY, c = col0 + tx + j * TX;
+            if (r < a.m && c < a.m) atomicAdd(C + (I * a.m + r) * a.ldo + J * a.m + c, coef * acc[i][j]);
+          }
+      }
+      __syncthreads();  // dl is rebuilt for the next leaf
+    }
+  }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+cudaError_t launch_tile(const Tables<T>& t, const SimtGemmArgs& a, cudaStream_t st) {
+  if (a.mp % BM || a.mp % BN || a.K % BK) return cudaErrorInvalidValue;
+  const int64_t gz = a.leaves < 65535 ? a.leaves : 65535;
+  const dim3 grid((unsigned)(a.mp / BN), (unsigned)(a.mp / BM), (unsigned)gz);
+  simt_gemm_kernel<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(t, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int simt_tile(int io, int64_t m) {
+  if (io == RBC_IO_F32) return m >= 256 ? 128 : 32;
+  return m >= 128 ? 64 : 32;
+}
+
+cudaError_t launch_simt_gemm(const Tables<float>& t, const SimtGemmArgs& a, cudaStream_t st) {
+  if (simt_tile(RBC_IO_F32, a.m) == 128) return launch_tile<float, 128, 128, 8, 8, 8>(t, a, st);
+  return launch_tile<float, 32, 32, 8, 2, 2>(t, a, st);
+}
+
+cudaError_t launch_simt_gemm(const Tables<double>& t, const SimtGemmArgs& a, cudaStream_t st) {
+  if (simt_tile(RBC_IO_F64, a.m) == 64) return launch_tile<double, 64, 64, 8, 4, 4>(t, a, st);
+  return launch_tile<double, 32, 32, 8, 2, 2>(t, a, st);
+}
+
+}  // namespace rbc

@@ -1,0 +1,365 @@
+// rbc_matmul: orchestration of one randomized recursive product C = F^(L)(A, B)
+// (Section 2.1.1, Eq. recursive-random-formula) on one stream:
+//   encode A and B level by level (root first) into the leaf operands,
+//   run the R^L leaf products, and decode (fused into the leaf epilogue, or level by level).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <memory>
+
+#include "convert.cuh"
+#include "level_kernels.cuh"
+#include "rbc_internal.h"
+#include "tc_gemm.cuh"
+
+namespace rbc {
+namespace {
+
+thread_local int64_t g_launches = 0;  // kernels launched by the current call
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool is_tc_leaf(int leaf) {
+  return leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_BF16 || leaf == RBC_LEAF_F16 ||
+         leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32;
+}
+
+int leaf_store(int leaf) {
+  switch (leaf) {
+    case RBC_LEAF_F64: return kStoreF64;
+    case RBC_LEAF_F32: return kStoreF32;
+    case RBC_LEAF_TF32:
+    case RBC_LEAF_3XTF32: return kStoreTF32;
+    case RBC_LEAF_BF16:
+    case RBC_LEAF_3XBF16: return kStoreBF16;
+    case RBC_LEAF_F16: return kStoreF16;
+  }
+  return -1;
+}
+
+size_t store_bytes(int s) { return s == kStoreF64 ? 8 : (s == kStoreBF16 || s == kStoreF16) ? 2 : 4; }
+
+struct Layout {
+  int64_t m = 0, mp = 0, K = 0;
+  int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 level by level
+  size_t es_io = 0, es_acc = 0, es_leaf = 0;
+  size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};
+  size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
+  size_t total = 0;
+};
+
+rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo) {
+  if (!p) return fail(RBC_EINVAL, "null plan");
+  if (io != RBC_IO_F32 && io != RBC_IO_F64) return fail(RBC_EINVAL, "bad io dtype");
+  if (leaf < RBC_LEAF_F64 || leaf > RBC_LEAF_3XTF32) return fail(RBC_EINVAL, "bad leaf dtype");
+  if (io == RBC_IO_F64 && leaf != RBC_LEAF_F64)
+    return fail(RBC_EUNSUPPORTED, "fp64 I/O supports the fp64 leaf mode only");
+  if (io == RBC_IO_F32 && leaf == RBC_LEAF_F64)
+    return fail(RBC_EUNSUPPORTED, "fp64 leaves with fp32 I/O are not implemented");
+  const int64_t blocks = ipow(p->n0, p->L);
+  if (N <= 0 || N % blocks) return fail(RBC_EINVAL, "N must be a positive multiple of n0^L");
+  const int L = p->L, R = p->R, n0 = p->n0;
+  lo->m = N / blocks;
+  lo->es_io = io == RBC_IO_F64 ? 8 : 4;
+  lo->es_acc = lo->es_io;
+  lo->store = leaf_store(leaf);
+  lo->es_leaf = store_bytes(lo->store);
+  lo->split = (leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32) ? 1 : 0;
+  if (is_tc_leaf(leaf)) {
+    lo->mp = tc_pad(lo->m);
+  } else {
+    const int tile = simt_tile(io, lo->m);
+    lo->mp = (lo->m + tile - 1) / tile * tile;
+  }
+  lo->K = lo->mp * (lo->split ? 3 : 1);
+  const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;
+  lo->decode = decode_req == 2 || !fused_ok ? 2 : 1;
+  if (decode_req == 1 && !fused_ok) return fail(RBC_EUNSUPPORTED, "fused decode needs <= 1024 draw sets");
+  if (lo->decode == 2 && is_tc_leaf(leaf) && !tc_supports_store_m())
+    return fail(RBC_EUNSUPPORTED, "level-by-level decode is not available for tensor-core leaves");
+  size_t off = 0;
+  for (int d = 1; d < L; ++d) {
+    const int64_t nd = lo->m * ipow(n0, L - d);
+    const size_t bytes = align256((size_t)ipow(R, d) * nd * nd * lo->es_io);
+    lo->encA[d] = off;
+    off += bytes;
+    lo->encB[d] = off;
+    off += bytes;
+  }
+  const int64_t leaves = ipow(R, L);
+  const size_t leaf_bytes = align256((size_t)leaves * lo->mp * lo->K * lo->es_leaf);
+  lo->leafS = off;
+  off += leaf_bytes;
+  lo->leafT = off;
+  off += leaf_bytes;
+  if (lo->decode == 2 && L > 0) {
+    lo->M = off;
+    off += align256((size_t)leaves * lo->mp * lo->mp * lo->es_acc);
+    for (int d = 1; d < L; ++d) {
+      const int64_t nd = lo->m * ipow(n0, L - d);
+      lo->dec[d] = off;
+      off += align256((size_t)ipow(R, d) * nd * nd * lo->es_acc);
+    }
+  }
+  lo->total = off;
+  return RBC_OK;
+}
+
+template <typename T>
+struct TablesBox {
+  std::unique_ptr<Tables<T>> t{new Tables<T>()};
+};
+
+// Encode one operand through all levels into the leaf operand buffer.
+template <typename T>
+rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
+                          int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st) {
+  const int L = p->L, R = p->R, n0 = p->n0;
+  const size_t* enc = tensor == 0 ? lo.encA : lo.encB;
+  char* leafbuf = ws + (tensor == 0 ? lo.leafS : lo.leafT);
+  if (L == 0) {  // identity "encode": conversion, padding, layout of the single leaf
+    rbc_status s = fill_tables(p, 0, 0, &tab);
+    if (s != RBC_OK) return s;
+    EncodeArgs a{};
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = leafbuf;
+    a.ldy = lo.K;
+    a.strideY = lo.mp * lo.K;
+    a.nb = lo.m;
+    a.rows_out = lo.mp;
+    a.cols_out = lo.mp;
+    a.parents = 1;
+    a.tensor = tensor;
+    a.trans = tensor == 1;
+    a.split = lo.split ? (tensor == 0 ? 1 : 2) : 0;
+    a.kpanel = lo.mp;
+    cudaError_t e = launch_encode_level(tab, a, 1, io, lo.store, st);
+    ++g_launches;
+    return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+  }
+  for (int d = 0; d < L; ++d) {
+    const int64_t n_par = lo.m * ipow(n0, L - d), nb = n_par / n0;
+    const int64_t parents = ipow(R, d);
+    const bool last = d == L - 1;
+    const int64_t chunk = p->scope == RBC_DRAW_PER_LEVEL ? parents : kMaxDraws;
+    for (int64_t c0 = 0; c0 < parents; c0 += chunk) {
+      const int64_t cnt = std::min(chunk, parents - c0);
+      const int64_t node_first = depth_start(R, d) + c0;
+      rbc_status s = p->scope == RBC_DRAW_PER_LEVEL ? fill_tables(p, d, 1, &tab)
+                                                    : fill_tables(p, node_first, cnt, &tab);
+      if (s != RBC_OK) return s;
+      EncodeArgs a{};
+      if (d == 0) {
+        a.X = X;
+        a.ldx = ldx;
+        a.strideX = 0;
+      } else {
+        a.X = ws + enc[d] + (size_t)c0 * n_par * n_par * lo.es_io;
+        a.ldx = n_par;
+        a.strideX = n_par * n_par;
+      }
+      if (last) {
+        a.Y = leafbuf + (size_t)c0 * R * lo.mp * lo.K * lo.es_leaf;
+        a.ldy = lo.K;
+        a.strideY = lo.mp * lo.K;
+        a.rows_out = lo.mp;
+        a.cols_out = lo.mp;
+        a.trans = tensor == 1;
+        a.split = lo.split ? (tensor == 0 ? 1 : 2) : 0;
+        a.kpanel = lo.mp;
+      } else {
+        a.Y = ws + enc[d + 1] + (size_t)c0 * R * nb * nb * lo.es_io;
+        a.ldy = nb;
+        a.strideY = nb * nb;
+        a.rows_out = nb;
+        a.cols_out = nb;
+      }
+      a.nb = nb;
+      a.parents = cnt;
+      a.node_first = node_first;
+      a.tensor = tensor;
+      const int store = last ? lo.store : (io == RBC_IO_F64 ? kStoreF64 : kStoreF32);
+      cudaError_t e = launch_encode_level(tab, a, n0, io, store, st);
+      ++g_launches;
+      if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+    }
+  }
+  return RBC_OK;
+}
+
+template <typename T>
+rbc_status decode_levels(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
+                         Tables<T>& tab, cudaStream_t st) {
+  const int L = p->L, R = p->R, n0 = p->n0;
+  for (int d = L - 1; d >= 0; --d) {
+    const int64_t n_par = lo.m * ipow(n0, L - d), nb = n_par / n0;
+    const int64_t parents = ipow(R, d);
+    const int64_t chunk = p->scope == RBC_DRAW_PER_LEVEL ? parents : kMaxDraws;
+    for (int64_t c0 = 0; c0 < parents; c0 += chunk) {
+      const int64_t cnt = std::min(chunk, parents - c0);
+      const int64_t node_first = depth_start(R, d) + c0;
+      rbc_status s = p->scope == RBC_DRAW_PER_LEVEL ? fill_tables(p, d, 1, &tab)
+                                                    : fill_tables(p, node_first, cnt, &tab);
+      if (s != RBC_OK) return s;
+      DecodeArgs a{};
+      if (d + 1 == L) {
+        a.M = ws + lo.M + (size_t)c0 * R * lo.mp * lo.mp * lo.es_acc;
+        a.ldm = lo.mp;
+        a.strideM = lo.mp * lo.mp;
+      } else {
+        a.M = ws + lo.dec[d + 1] + (size_t)c0 * R * nb * nb * lo.es_acc;
+        a.ldm = nb;
+        a.strideM = nb * nb;
+      }
+      if (d == 0) {
+        a.P = C;
+        a.ldp = ldc;
+        a.strideP = 0;
+      } else {
+        a.P = ws + lo.dec[d] + (size_t)c0 * n_par * n_par * lo.es_acc;
+        a.ldp = n_par;
+        a.strideP = n_par * n_par;
+      }
+      a.nb = nb;
+      a.parents = cnt;
+      a.node_first = node_first;
+      cudaError_t e = launch_decode_level(tab, a, n0, st);
+      ++g_launches;
+      if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+    }
+  }
+  return RBC_OK;
+}
+
+inline void mark(const rbc_matmul_opts* o, int i, cudaStream_t st) {
+  if (o && o->events[i]) cudaEventRecord(static_cast<cudaEvent_t>(o->events[i]), st);
+}
+
+template <typename T>
+rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void* B, void* C, int64_t N,
+               int64_t lda, int64_t ldb, int64_t ldc, int io, int leaf, char* ws, cudaStream_t st,
+               const rbc_matmul_opts* opts) {
+  static thread_local TablesBox<T> box;
+  Tables<T>& tab = *box.t;
+  mark(opts, 0, st);
+  rbc_status s = encode_operand<T>(p, lo, io, 0, A, lda, ws, tab, st);
+  if (s != RBC_OK) return s;
+  s = encode_operand<T>(p, lo, io, 1, B, ldb, ws, tab, st);
+  if (s != RBC_OK) return s;
+  const int L = p->L;
+  const int64_t leaves = ipow(p->R, L);
+  const bool fused = lo.decode == 1 || L == 0;
+  if (fused && L > 0) {
+    cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * lo.es_io, 0, (size_t)N * lo.es_io, (size_t)N, st);
+    if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  }
+  mark(opts, 1, st);
+  if (fused) {
+    s = p->scope == RBC_DRAW_PER_LEVEL ? fill_tables(p, 0, p->draw_count, &tab)
+                                       : fill_tables(p, 0, p->draw_count, &tab);
+  } else {
+    s = fill_tables(p, 0, 0, &tab);
+  }
+  if (s != RBC_OK) return s;
+  if (is_tc_leaf(leaf)) {
+    TcGemmArgs g{};
+    g.S = ws + lo.leafS;
+    g.Tt = ws + lo.leafT;
+    g.K = lo.K;
+    g.m = lo.m;
+    g.mp = lo.mp;
+    g.leaves = leaves;
+    g.C = C;
+    g.ldc = ldc;
+    g.direct = L == 0;
+    g.leaf = leaf;
+    if constexpr (sizeof(T) == 4) {
+      cudaError_t e = launch_tc_gemm(tab, g, st);
+      ++g_launches;
+      if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+    } else {
+      return fail(RBC_EUNSUPPORTED, "tensor-core leaves need fp32 I/O");
+    }
+  } else {
+    SimtGemmArgs g{};
+    g.S = ws + lo.leafS;
+    g.Tt = ws + lo.leafT;
+    g.lds = lo.K;
+    g.ldt = lo.K;
+    g.strideS = lo.mp * lo.K;
+    g.strideT = lo.mp * lo.K;
+    g.K = lo.K;
+    g.m = lo.m;
+    g.mp = lo.mp;
+    g.leaves = leaves;
+    if (fused) {
+      g.out = C;
+      g.ldo = ldc;
+      g.mode = L == 0 ? 2 : 1;
+    } else {
+      g.out = ws + lo.M;
+      g.ldo = lo.mp;
+      g.strideO = lo.mp * lo.mp;
+      g.mode = 0;
+    }
+    cudaError_t e = launch_simt_gemm(tab, g, st);
+    ++g_launches;
+    if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  }
+  mark(opts, 2, st);
+  if (!fused) {
+    s = decode_levels<T>(p, lo, C, ldc, ws, tab, st);
+    if (s != RBC_OK) return s;
+  }
+  mark(opts, 3, st);
+  return RBC_OK;
+}
+
+}  // namespace
+}  // namespace rbc
+
+using namespace rbc;
+
+extern "C" {
+
+size_t rbc_workspace_size_ex(rbc_plan_t plan, int64_t N, int io, int leaf, const rbc_matmul_opts* o) {
+  Layout lo;
+  if (make_layout(plan, N, io, leaf, o ? o->decode : 0, &lo) != RBC_OK) return 0;
+  return lo.total;
+}
+
+size_t rbc_workspace_size(rbc_plan_t plan, int64_t N, int io, int leaf) {
+  return rbc_workspace_size_ex(plan, N, io, leaf, nullptr);
+}
+
+rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N,
+                         int64_t lda, int64_t ldb, int64_t ldc, int io, int leaf, void* workspace,
+                         size_t ws_bytes, void* stream, rbc_matmul_opts* opts) {
+  if (!plan || !A || !B || !C) return fail(RBC_EINVAL, "null argument");
+  if (opts && (opts->decode < 0 || opts->decode > 2)) return fail(RBC_EINVAL, "bad decode option");
+  Layout lo;
+  rbc_status s = make_layout(plan, N, io, leaf, opts ? opts->decode : 0, &lo);
+  if (s != RBC_OK) return s;
+  if (lda < N || ldb < N || ldc < N) return fail(RBC_EINVAL, "leading dimension smaller than N");
+  if (lo.total > 0 && (!workspace || ((uintptr_t)workspace & 255)))
+    return fail(RBC_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (ws_bytes < lo.total) return fail(RBC_ENOMEM, "workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  g_launches = 0;
+  if (io == RBC_IO_F64)
+    s = run<double>(plan, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
+  else
+    s = run<float>(plan, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
+  if (opts) opts->launches = g_launches;
+  return s;
+}
+
+rbc_status rbc_matmul(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N, int64_t lda,
+                      int64_t ldb, int64_t ldc, int io, int leaf, void* workspace, size_t ws_bytes,
+                      void* stream) {
+  return rbc_matmul_ex(plan, A, B, C, N, lda, ldb, ldc, io, leaf, workspace, ws_bytes, stream, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,212 @@
+"""ctypes binding of librbc (include/rbc.h): the same entry points, argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts Python/torch
+arguments to pointers and sizes and turns non-zero statuses into exceptions.  There is no
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+# enums (include/rbc.h)
+RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_ETIMEOUT, RBC_EBUSY, RBC_EKAPPA, RBC_EUNSUPPORTED = range(8)
+IO_F64, IO_F32 = 0, 1
+LEAF_F64, LEAF_F32, LEAF_TF32, LEAF_BF16, LEAF_F16, LEAF_3XBF16, LEAF_3XTF32 = range(7)
+RAND_FULL, RAND_SIGN, RAND_PERM, RAND_NONE = range(4)
+DRAW_PER_NODE, DRAW_PER_LEVEL = 0, 1
+LEAF_NAMES = {"f64": LEAF_F64, "f32": LEAF_F32, "tf32": LEAF_TF32, "bf16": LEAF_BF16,
+              "f16": LEAF_F16, "3xbf16": LEAF_3XBF16, "3xtf32": LEAF_3XTF32}
+
+
+class rbc_plan_desc(C.Structure):
+    _fields_ = [("U", C.POINTER(C.c_double)), ("V", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
+                ("R", C.c_int), ("n0", C.c_int), ("levels", C.c_int), ("seed", C.c_uint64),
+                ("rand_mode", C.c_int), ("draw_scope", C.c_int), ("rescale_kappa", C.c_int)]
+
+
+class rbc_plan_info(C.Structure):
+    _fields_ = [("R", C.c_int), ("n0", C.c_int), ("levels", C.c_int), ("rand_mode", C.c_int),
+                ("draw_scope", C.c_int), ("draw_count", C.c_int64), ("leaf_count", C.c_int64),
+                ("kappa", C.c_double), ("tau", C.c_double), ("gamma", C.c_double),
+                ("scale", C.c_double), ("seed", C.c_uint64)]
+
+
+class rbc_matmul_opts(C.Structure):
+    _fields_ = [("decode", C.c_int), ("reserved", C.c_int * 7), ("events", C.c_void_p * 4),
+                ("launches", C.c_int64)]
+
+
+# name -> (restype, argtypes): every function include/rbc.h declares
+_P = C.c_void_p
+SIGNATURES = {
+    "rbc_plan_create": (C.c_int, [C.POINTER(C.c_double)] * 3 + [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_P)]),
+    "rbc_plan_create_ex": (C.c_int, [C.POINTER(rbc_plan_desc), C.POINTER(_P)]),
+    "rbc_plan_destroy": (None, [_P]),
+    "rbc_plan_query": (C.c_int, [_P, C.POINTER(rbc_plan_info)]),
+    "rbc_plan_draws": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(C.c_int8), C.POINTER(C.c_int8)]),
+    "rbc_plan_tables": (C.c_int, [_P, C.c_int64] + [C.POINTER(C.c_double)] * 3),
+    "rbc_workspace_size": (C.c_size_t, [_P, C.c_int64, C.c_int, C.c_int]),
+    "rbc_workspace_size_ex": (C.c_size_t, [_P, C.c_int64, C.c_int, C.c_int, C.POINTER(rbc_matmul_opts)]),
+    "rbc_matmul": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                             _P, C.c_size_t, _P]),
+    "rbc_matmul_ex": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                                _P, C.c_size_t, _P, C.POINTER(rbc_matmul_opts)]),
+    "rbc_norms": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P,
+                            C.c_size_t, _P]),
+    "rbc_norms_work_size": (C.c_size_t, []),
+    "rbc_status_string": (C.c_char_p, [C.c_int]),
+    "rbc_last_error": (C.c_char_p, []),
+    "rbc_version": (C.c_int, []),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded librbc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_1905_07439_gb300.build.build()")
+        L = C.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RbcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.rbc_last_error().decode()
+        super().__init__(f"{where}: {L.rbc_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != RBC_OK:
+        raise RbcError(status, where)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Plan:
+    """Owner of an rbc_plan_t (rbc_plan_create_ex)."""
+
+    def __init__(self, U, V, W, levels: int, seed: int = 0, rand_mode: int = RAND_FULL,
+                 draw_scope: int = DRAW_PER_NODE, rescale_kappa: int = -1):
+        L = lib()
+        self._keep = [np.ascontiguousarray(np.asarray(t, dtype=np.float64)) for t in (U, V, W)]
+        U_, V_, W_ = self._keep
+        n0, n0b, R = U_.shape
+        if n0 != n0b or V_.shape != U_.shape or W_.shape != U_.shape:
+            raise ValueError("U, V, W must all have shape (n0, n0, R)")
+        d = rbc_plan_desc(_dptr(U_), _dptr(V_), _dptr(W_), R, n0, levels, seed & (2**64 - 1),
+                          rand_mode, draw_scope, rescale_kappa)
+        h = _P()
+        check(L.rbc_plan_create_ex(C.byref(d), C.byref(h)), "rbc_plan_create_ex")
+        self.handle = h
+        self.n0, self.R, self.levels = n0, R, levels
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib().rbc_plan_destroy(h)
+            self.handle = None
+
+    def info(self) -> dict:
+        i = rbc_plan_info()
+        check(lib().rbc_plan_query(self.handle, C.byref(i)), "rbc_plan_query")
+        return {f: getattr(i, f) for f, _ in rbc_plan_info._fields_}
+
+    def draws(self, first: int = 0, count: int | None = None):
+        info = self.info()
+        count = info["draw_count"] - first if count is None else count
+        perms = np.zeros((count, 3, self.n0), dtype=np.int8)
+        signs = np.zeros((count, 3, self.n0), dtype=np.int8)
+        check(lib().rbc_plan_draws(self.handle, first, count,
+                                   perms.ctypes.data_as(C.POINTER(C.c_int8)),
+                                   signs.ctypes.data_as(C.POINTER(C.c_int8))), "rbc_plan_draws")
+        return perms, signs
+
+    def tables(self, key: int):
+        out = [np.zeros((self.n0, self.n0, self.R)) for _ in range(3)]
+        check(lib().rbc_plan_tables(self.handle, key, *[_dptr(t) for t in out]), "rbc_plan_tables")
+        return tuple(out)
+
+    def workspace_size(self, N: int, io: int, leaf: int, decode: int = 0) -> int:
+        o = rbc_matmul_opts(decode)
+        return int(lib().rbc_workspace_size_ex(self.handle, N, io, leaf, C.byref(o)))
+
+
+def _io_of(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return IO_F64
+    if t.dtype == torch.float32:
+        return IO_F32
+    raise TypeError("A, B, C must be float32 or float64 CUDA tensors")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def matmul(plan: Plan, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, stream=None,
+           decode: int = 0, events=None):
+    """C = F^(L)(A, B) through rbc_matmul_ex on torch CUDA tensors (row-major, unit column stride)."""
+    import torch
+    N = A.shape[0]
+    if A.shape != (N, N) or B.shape != (N, N):
+        raise ValueError("square N x N inputs required")
+    if A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("A and B need unit column stride")
+    io = _io_of(A)
+    if _io_of(B) != io:
+        raise TypeError("A and B must have the same dtype")
+    if C_out is None:
+        C_out = torch.empty((N, N), dtype=A.dtype, device=A.device)
+    need = plan.workspace_size(N, io, leaf, decode)
+    if need == 0 and N > 0:
+        # let the library report why (invalid combination)
+        pass
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
+    o = rbc_matmul_opts(decode)
+    if events is not None:
+        for i, ev in enumerate(events):
+            o.events[i] = ev.cuda_event if ev is not None else None
+    check(lib().rbc_matmul_ex(plan.handle, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), N,
+                              A.stride(0), B.stride(0), C_out.stride(0), io, leaf,
+                              workspace.data_ptr(), workspace.numel(), _stream_ptr(stream), C.byref(o)),
+          "rbc_matmul_ex")
+    return C_out
+
+
+def norms(X, Y=None, stream=None, work=None, out=None):
+    """(sum (X-Y)^2, sum Y^2) in fp64 via rbc_norms (device reduction); returns a 2-element
+    float64 CUDA tensor."""
+    import torch
+    rows, cols = X.shape
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=X.device)
+    if work is None:
+        work = torch.empty(int(lib().rbc_norms_work_size()), dtype=torch.uint8, device=X.device)
+    yt = _io_of(Y) if Y is not None else 0
+    check(lib().rbc_norms(X.data_ptr(), Y.data_ptr() if Y is not None else None, rows, cols,
+                          X.stride(0), Y.stride(0) if Y is not None else 0, _io_of(X), yt,
+                          out.data_ptr(), work.data_ptr(), work.numel(), _stream_ptr(stream)),
+          "rbc_norms")
+    return out

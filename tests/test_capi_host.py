@@ -1,0 +1,119 @@
+"""Host-side checks of the C-ABI library (no GPU): every symbol include/rbc.h declares is
+exported, plan validation and error codes, and bit-exact agreement of the library's draws
+and expanded tables (Prop. 10) with the oracle's independent implementation."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import rbc_oracle as o
+from rbc_inputs import laderman, perturbed, strassen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rbc():
+    from paper_1905_07439_gb300 import build as b
+    b.build()
+    import paper_1905_07439_gb300 as pkg
+    return pkg
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(rbc_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(rbc):
+    L = rbc.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(L, name), name
+    # and the binding knows every one of them
+    assert set(declared) <= set(rbc.SIGNATURES), set(declared) - set(rbc.SIGNATURES)
+    assert L.rbc_version() >= 100
+
+
+def test_status_strings(rbc):
+    L = rbc.lib()
+    for s in range(8):
+        assert L.rbc_status_string(s)
+
+
+def test_plan_validation_errors(rbc):
+    U, V, W = strassen()
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.Plan(U, V, 0.0 * W, levels=1)          # kappa == 1
+    assert e.value.status == 6
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.Plan(U, V, W, levels=9)
+    assert e.value.status == 1
+    with pytest.raises(rbc.RbcError):
+        rbc.Plan(U, V, W, levels=1, rand_mode=7)
+    Ub = U.copy()
+    Ub[0, 0, 0] = np.nan
+    with pytest.raises(rbc.RbcError):
+        rbc.Plan(Ub, V, W, levels=1)
+
+
+@pytest.mark.parametrize("fn,L,mode,scope", [
+    (strassen, 2, o.RAND_FULL, o.DRAW_PER_NODE),
+    (strassen, 4, o.RAND_FULL, o.DRAW_PER_NODE),
+    (laderman, 3, o.RAND_FULL, o.DRAW_PER_NODE),
+    (strassen, 3, o.RAND_SIGN, o.DRAW_PER_LEVEL),
+    (laderman, 2, o.RAND_PERM, o.DRAW_PER_NODE),
+    (strassen, 2, o.RAND_NONE, o.DRAW_PER_NODE),
+])
+def test_draws_bit_exact_vs_oracle(rbc, fn, L, mode, scope):
+    U, V, W = fn()
+    seed = 0xDEADBEEF12345
+    p = rbc.Plan(U, V, W, levels=L, seed=seed, rand_mode=mode, draw_scope=scope)
+    info = p.info()
+    op = o.Plan(U, V, W, levels=L, seed=seed, mode=mode, scope=scope)
+    n_draws = L if scope == o.DRAW_PER_LEVEL else op.node_count()
+    assert info["draw_count"] == n_draws
+    assert info["leaf_count"] == op.R ** L
+    perms, signs = p.draws()
+    for key in range(n_draws):
+        d = o.node_draw(seed, key, op.n0, mode)
+        assert [tuple(x) for x in perms[key]] == [tuple(x) for x in d.pi], key
+        assert [tuple(x) for x in signs[key]] == [tuple(x) for x in d.s], key
+
+
+@pytest.mark.parametrize("fn", [strassen, laderman])
+def test_tables_bit_exact_vs_oracle(rbc, fn):
+    U, V, W = perturbed(*fn(), seed=3, std=1e-3)
+    p = rbc.Plan(U, V, W, levels=2, seed=77)
+    op = o.Plan(U, V, W, levels=2, seed=77)
+    info = p.info()
+    assert info["kappa"] == op.kappa          # same sequential fp64 loop order
+    assert abs(info["tau"] - o.tau(U, V, W)) <= 1e-15 * max(1.0, info["tau"])
+    assert abs(info["gamma"] - o.gamma(U, V, W)) <= 1e-14 * info["gamma"]
+    assert info["scale"] == op.scale
+    for key in range(info["draw_count"]):
+        got = p.tables(key)
+        want = o.expand_tables(U, V, W, o.node_draw(77, key, op.n0, o.RAND_FULL), op.scale)
+        for g, w_ in zip(got, want):
+            assert np.array_equal(g, w_), key
+
+
+def test_workspace_sizes(rbc):
+    U, V, W = strassen()
+    p = rbc.Plan(U, V, W, levels=2)
+    assert p.workspace_size(128, rbc.IO_F64, rbc.LEAF_F64) > 0
+    assert p.workspace_size(130, rbc.IO_F64, rbc.LEAF_F64) == 0       # not a multiple of 4
+    assert p.workspace_size(128, rbc.IO_F64, rbc.LEAF_BF16) == 0      # fp64 I/O, bf16 leaves
+    fused = p.workspace_size(4096, rbc.IO_F32, rbc.LEAF_F32, decode=1)
+    staged = p.workspace_size(4096, rbc.IO_F32, rbc.LEAF_F32, decode=2)
+    assert staged > fused > 0
+    # fused fp32 leaves: level-1 encode (7 x 2048^2 each side) + leaves (49 x 1024^2 each side)
+    assert fused >= 4 * (2 * 7 * 2048**2 + 2 * 49 * 1024**2)

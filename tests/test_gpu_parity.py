@@ -1,0 +1,122 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
+inputs and the same draws (Section 2.1.1 recursion, Prop. 10 tables).
+
+Gates: fp64 leaves (fp64 I/O) relative Frobenius error <= 1e-12 against the oracle's
+computation with the same draws; lower precisions the normwise gate of tests/_helpers.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import rbc_oracle as o
+from rbc_inputs import gaussian, matrix_pair
+
+from ._helpers import formula, gate, gpu_rbc, normwise, oracle_plan, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rbc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1905_07439_gb300 import build as b
+    b.build()
+    import paper_1905_07439_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("decode", [1, 2])
+def test_strassen_n128_l2_fp64_seed0(rbc, decode):
+    # Randomized Strassen, 2 levels, N = 128, fp64, seed 0, per-node draws, 32 x 32 leaves.
+    U, V, W = formula("strassen")
+    A, B = gaussian(128, 0), gaussian(128, 1)
+    plan = rbc.Plan(U, V, W, levels=2, seed=0)
+    C = gpu_rbc(rbc, plan, A, B, torch.float64, rbc.LEAF_F64, decode)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, 2, 0))
+    assert rel(C, ref) <= 1e-12
+    assert rel(C, A @ B) <= 1e-12
+
+
+CASES_F64 = [
+    # formula, L, N (ragged leaf sizes), mode, scope
+    ("strassen", 0, 45, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("strassen", 1, 74, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("strassen", 2, 148, o.RAND_FULL, o.DRAW_PER_LEVEL),
+    ("strassen", 3, 88, o.RAND_SIGN, o.DRAW_PER_NODE),
+    ("strassen", 4, 16 * 9, o.RAND_PERM, o.DRAW_PER_NODE),
+    ("strassen", 2, 4, o.RAND_FULL, o.DRAW_PER_NODE),          # m = 1
+    ("laderman", 1, 3 * 70, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("laderman", 2, 9 * 13, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("laderman", 3, 27 * 5, o.RAND_NONE, o.DRAW_PER_NODE),
+    ("noisy-strassen", 1, 2 * 130, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("noisy-strassen", 3, 8 * 17, o.RAND_FULL, o.DRAW_PER_LEVEL),
+    ("noisy-laderman", 2, 9 * 11, o.RAND_FULL, o.DRAW_PER_NODE),
+]
+
+
+@pytest.mark.parametrize("decode", [1, 2])
+@pytest.mark.parametrize("name,L,N,mode,scope", CASES_F64)
+def test_fp64_leaves_match_oracle(rbc, name, L, N, mode, scope, decode):
+    U, V, W = formula(name, seed=1)
+    A, B = matrix_pair("normal", N, seed=10 + L)
+    seed = 1234 + N
+    plan = rbc.Plan(U, V, W, levels=L, seed=seed, rand_mode=mode, draw_scope=scope)
+    C = gpu_rbc(rbc, plan, A, B, torch.float64, rbc.LEAF_F64, decode)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, seed, mode, scope))
+    assert rel(C, ref) <= 1e-12
+
+
+CASES_F32 = [
+    ("strassen", 1, 2 * 300, "normal"),
+    ("strassen", 2, 4 * 300, "normal"),
+    ("strassen", 2, 4 * 300, "hard"),
+    ("strassen", 3, 8 * 45, "normal"),
+    ("laderman", 2, 9 * 100, "normal"),
+    ("noisy-strassen", 2, 4 * 260, "normal"),
+]
+
+
+@pytest.mark.parametrize("decode", [1, 2])
+@pytest.mark.parametrize("name,L,N,dist", CASES_F32)
+def test_fp32_leaves_match_oracle(rbc, name, L, N, dist, decode):
+    U, V, W = formula(name, seed=2)
+    A, B = matrix_pair(dist, N, seed=20 + L)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    plan = rbc.Plan(U, V, W, levels=L, seed=99)
+    C = gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_F32, decode)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, 99))
+    assert normwise(C, ref, A, B) <= gate("f32", U.shape[0], L, N)
+
+
+def test_argument_errors(rbc):
+    U, V, W = formula("strassen")
+    plan = rbc.Plan(U, V, W, levels=2)
+    A = torch.zeros((130, 130), dtype=torch.float64, device="cuda")
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.matmul(plan, A, A, leaf=rbc.LEAF_F64)
+    assert e.value.status == 1
+    A = torch.zeros((128, 128), dtype=torch.float64, device="cuda")
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.matmul(plan, A, A, leaf=rbc.LEAF_F64, workspace=ws)
+    assert e.value.status == 2
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.matmul(plan, A, A, leaf=rbc.LEAF_BF16)
+    assert e.value.status == 7
+
+
+def test_norms_match_numpy(rbc):
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((333, 517))
+    Y = rng.standard_normal((333, 517))
+    Xt = torch.tensor(X, device="cuda")
+    Yt = torch.tensor(Y, device="cuda", dtype=torch.float32)
+    out = rbc.norms(Xt, Yt).cpu().numpy()
+    Yf = Y.astype(np.float32).astype(np.float64)
+    assert np.isclose(out[0], np.sum((X - Yf) ** 2), rtol=1e-12)
+    assert np.isclose(out[1], np.sum(Yf**2), rtol=1e-12)
+    out2 = rbc.norms(Xt).cpu().numpy()
+    assert np.isclose(out2[0], np.sum(X**2), rtol=1e-12) and out2[1] == 0.0
+    # deterministic: repeated calls are bit-identical
+    assert np.array_equal(rbc.norms(Xt, Yt).cpu().numpy(), out)
