@@ -175,6 +175,13 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
                          void* workspace, size_t workspace_bytes, void* stream,
                          rbc_matmul_opts* opts);
 
+/* Device-side status of the calls that used `workspace` (its first 4 bytes, cleared by every
+ * rbc_matmul): waits for `stream`, copies the word to *device_status and clears it.  0 means
+ * no error; RBC_ETIMEOUT means a bounded wait inside a kernel expired and that kernel skipped
+ * its remaining work (the result is then invalid).  Returns the word as a status.
+ * Synchronizes the stream. */
+rbc_status rbc_workspace_check(void* workspace, void* stream, int* device_status);
+
 /* Frobenius reductions in fp64 (Section 3's relative errors): out[0] = sum (X - Y)^2,
  * out[1] = sum Y^2 (Y == NULL: out[0] = sum X^2, out[1] = 0).  X, Y: device, rows x cols
  * row-major with lds ldx, ldy, element types rbc_io_dtype.  out: device, 2 doubles.

@@ -106,13 +106,12 @@ __global__ void __launch_bounds__(256) encode_level_kernel(const __grid_constant
         if (a.split == 0) {
           dst[0] = to_store<S>((double)v[q]);
         } else {
+          // split compensated leaves: x = hi + lo with hi = round(x), lo = round(x - hi),
+          // stored as two panels [hi | lo] along the row
           const Tout hi = to_store<S>((double)v[q]);
           const Tout lo = to_store<S>((double)(v[q] - (Tc)from_store<S>(hi)));
-          // left operand panels [hi | hi | lo], right operand panels [hi | lo | hi]:
-          // the product over the tripled inner dimension is hi*hi' + hi*lo' + lo*hi'.
           dst[0] = hi;
-          dst[a.kpanel] = a.split == 1 ? hi : lo;
-          dst[2 * a.kpanel] = a.split == 1 ? lo : hi;
+          dst[a.kpanel] = lo;
         }
       }
     }

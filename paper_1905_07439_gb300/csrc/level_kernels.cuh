@@ -19,7 +19,7 @@ struct EncodeArgs {
   int64_t node_first;   // heap id of parent 0
   int tensor;           // 0: left operand (u^), 1: right operand (v^)
   int trans;            // 1: write each child transposed
-  int split;            // 0: plain; 1: left split panels [hi|hi|lo]; 2: right [hi|lo|hi]
+  int split;            // 0: plain; 1: split panels [hi | lo] (hi = round(x), lo = round(x - hi))
   int64_t kpanel;       // column offset between split panels
 };
 

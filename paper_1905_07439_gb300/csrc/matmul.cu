@@ -17,6 +17,8 @@ namespace {
 
 thread_local int64_t g_launches = 0;  // kernels launched by the current call
 
+constexpr size_t kStatusBytes = 256;
+
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool is_tc_leaf(int leaf) {
@@ -71,13 +73,13 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     const int tile = simt_tile(io, lo->m);
     lo->mp = (lo->m + tile - 1) / tile * tile;
   }
-  lo->K = lo->mp * (lo->split ? 3 : 1);
+  lo->K = lo->mp * (lo->split ? 2 : 1);
   const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;
   lo->decode = decode_req == 2 || !fused_ok ? 2 : 1;
   if (decode_req == 1 && !fused_ok) return fail(RBC_EUNSUPPORTED, "fused decode needs <= 1024 draw sets");
   if (lo->decode == 2 && is_tc_leaf(leaf) && !tc_supports_store_m())
     return fail(RBC_EUNSUPPORTED, "level-by-level decode is not available for tensor-core leaves");
-  size_t off = 0;
+  size_t off = kStatusBytes;  // device status word(s) first
   for (int d = 1; d < L; ++d) {
     const int64_t nd = lo->m * ipow(n0, L - d);
     const size_t bytes = align256((size_t)ipow(R, d) * nd * nd * lo->es_io);
@@ -132,7 +134,7 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
     a.parents = 1;
     a.tensor = tensor;
     a.trans = tensor == 1;
-    a.split = lo.split ? (tensor == 0 ? 1 : 2) : 0;
+    a.split = lo.split;
     a.kpanel = lo.mp;
     cudaError_t e = launch_encode_level(tab, a, 1, io, lo.store, st);
     ++g_launches;
@@ -166,7 +168,7 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
         a.rows_out = lo.mp;
         a.cols_out = lo.mp;
         a.trans = tensor == 1;
-        a.split = lo.split ? (tensor == 0 ? 1 : 2) : 0;
+        a.split = lo.split;
         a.kpanel = lo.mp;
       } else {
         a.Y = ws + enc[d + 1] + (size_t)c0 * R * nb * nb * lo.es_io;
@@ -273,7 +275,10 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
     g.C = C;
     g.ldc = ldc;
     g.direct = L == 0;
+    g.store_m = !fused;
+    g.M = fused ? nullptr : ws + lo.M;
     g.leaf = leaf;
+    g.status = reinterpret_cast<int*>(ws);
     if constexpr (sizeof(T) == 4) {
       cudaError_t e = launch_tc_gemm(tab, g, st);
       ++g_launches;
@@ -348,12 +353,28 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
   g_launches = 0;
+  {
+    cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);  // clear the status word
+    if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  }
   if (io == RBC_IO_F64)
     s = run<double>(plan, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
   else
     s = run<float>(plan, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
   if (opts) opts->launches = g_launches;
   return s;
+}
+
+rbc_status rbc_workspace_check(void* workspace, void* stream, int* device_status) {
+  if (!workspace || !device_status) return fail(RBC_EINVAL, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, workspace, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
+  if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  *device_status = v;
+  return v == 0 ? RBC_OK : fail((rbc_status)v, "a kernel of a previous call reported an error");
 }
 
 rbc_status rbc_matmul(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N, int64_t lda,

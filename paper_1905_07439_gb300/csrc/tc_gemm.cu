@@ -1,9 +1,385 @@
+// Leaf products M_rho = S_rho T_rho (Section 2.1.1, F^(0) the standard product) on the
+// 5th-generation tensor cores, batched over all R^L leaves, with the decode of
+// Eq. recursive-random-formula fused into the epilogue.
+//
+// Persistent, warp-specialized kernel, one CTA per SM (192 threads):
+//   warp 0     one thread issues TMA loads of the K-major S and T^T tiles (128-byte swizzle)
+//              into a ring of shared-memory stages (mbarrier full/empty handshake);
+//   warp 1     allocates TMEM (two fp32 accumulators of 128 x BN) and one thread issues
+//              tcgen05.mma (M = 128, N = BN, K = 16 bf16/f16 or 8 tf32 per instruction),
+//              committing stage releases and accumulator-ready signals;
+//   warps 2-5  drain an accumulator with tcgen05.ld (one TMEM lane = one tile row per
+//              thread) while the MMA fills the other, and scatter the tile into every C block
+//              it feeds: C_IJ += (prod_d w^(node_d)_{i_d j_d r_d}) * M_tile, by 16-byte
+//              vector reductions into the zeroed C (or plain stores when L = 0 / stored M).
+// Split-compensated modes keep hi and lo panels of each operand in a stage and issue
+// hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator.
+// Every mbarrier wait is bounded (2 s); on expiry the kernel records RBC_ETIMEOUT in the
+// workspace status word, drains its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "decode_dest.cuh"
+#include "ptx.cuh"
 #include "tc_gemm.cuh"
 
 namespace rbc {
-int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
-bool tc_supports_store_m() { return false; }
-cudaError_t launch_tc_gemm(const Tables<float>&, const TcGemmArgs&, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int BM = 128;
+constexpr int kRowBytes = 128;  // one swizzle row: 64 bf16/f16 or 32 tf32 elements of K
+constexpr int kThreads = 192;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+struct Params {
+  int64_t m, mp, leaves, total_tiles;
+  int nk, tiles_m, tiles_n;
+  int kpanel;      // element offset of the lo panel along K (split modes)
+  uint32_t idesc;
+  int epi;         // 0: fused decode by reductions, 1: direct store (L = 0), 2: store M
+  int vec_ok;      // 16-byte vector access to C allowed
+  float* C;
+  int64_t ldc;
+  float* M;
+  int64_t ldm, strideM;
+  int* status;
+};
+
+template <int STAGES>
+struct Aux {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+  DestList<float> dl[4];
+};
+
+__device__ __forceinline__ void raise_abort(volatile int* abort, int* status) {
+  *abort = 1;
+  if (status) atomicExch(status, (int)RBC_ETIMEOUT);
 }
+
+__device__ __forceinline__ void tile_coords(int64_t tile, const Params& p, int64_t* leaf, int* tm, int* tn) {
+  const int64_t per_leaf = (int64_t)p.tiles_m * p.tiles_n;
+  *leaf = tile / per_leaf;
+  const int r = (int)(tile - *leaf * per_leaf);
+  *tm = r / p.tiles_n;
+  *tn = r - *tm * p.tiles_n;
+}
+
+template <int KIND, int SPLIT, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ Tables<float> t, const Params p) {
+  constexpr int P = SPLIT ? 2 : 1;
+  constexpr uint32_t A_BYTES = BM * kRowBytes, B_BYTES = BN * kRowBytes;
+  constexpr uint32_t STAGE_BYTES = P * (A_BYTES + B_BYTES);
+  constexpr int KSTEPS = kRowBytes / 32;  // MMA K steps of 32 bytes per stage
+  constexpr int KELEM = KIND == 0 ? 64 : 32;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Aux<STAGES>* aux = reinterpret_cast<Aux<STAGES>*>(smem + STAGES * STAGE_BYTES);
+  volatile int* abort = &aux->abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&aux->full[s], 1);
+      ptx::mbar_init(&aux->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&aux->tfull[b], 1);
+      ptx::mbar_init(&aux->tempty[b], 4);
+    }
+    ptx::mbar_init(&aux->drain, 1);
+    aux->abort = 0;
+    ptx::fence_mbar_init();
+    ptx::prefetch_tmap(&tmA);
+    ptx::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(&aux->tmem_base, 2 * BN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = aux->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t armed = 0, last_par = 0;  // per-stage bit masks for the teardown drain
+      for (int64_t tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+        int64_t leaf;
+        int tm, tn;
+        tile_coords(tile, p, &leaf, &tm, &tn);
+        const int32_t rowA = (int32_t)(leaf * p.mp + (int64_t)tm * BM);
+        const int32_t rowB = (int32_t)(leaf * p.mp + (int64_t)tn * BN);
+        for (int kb = 0; kb < p.nk; ++kb) {
+          if (!ptx::wait_bounded(&aux->empty[s], ph ^ 1u, abort, kWaitNs)) {
+            raise_abort(abort, p.status);
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(&aux->full[s], STAGE_BYTES);
+          const int32_t kx = kb * KELEM;
+          ptx::tma_load_2d(st, &tmA, &aux->full[s], kx, rowA);
+          if (SPLIT) ptx::tma_load_2d(st + A_BYTES, &tmA, &aux->full[s], kx + p.kpanel, rowA);
+          ptx::tma_load_2d(st + P * A_BYTES, &tmB, &aux->full[s], kx, rowB);
+          if (SPLIT) ptx::tma_load_2d(st + P * A_BYTES + B_BYTES, &tmB, &aux->full[s], kx + p.kpanel, rowB);
+          armed |= 1u << s;
+          last_par = (last_par & ~(1u << s)) | (ph << s);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      // Wait for every copy this thread started (bounded) before the CTA can exit.
+      for (int q = 0; q < STAGES; ++q)
+        if (armed & (1u << q)) {
+          volatile int never = 0;
+          ptx::wait_bounded(&aux->full[q], (last_par >> q) & 1u, &never, kWaitNs);
+        }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int s = 0, buf = 0;
+      uint32_t ph = 0, aph = 0;
+      for (int64_t tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+        if (!ptx::wait_bounded(&aux->tempty[buf], aph ^ 1u, abort, kWaitNs)) {
+          raise_abort(abort, p.status);
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int kb = 0; kb < p.nk; ++kb) {
+          if (!ptx::wait_bounded(&aux->full[s], ph, abort, kWaitNs)) {
+            raise_abort(abort, p.status);
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t a0 = ptx::smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t b0 = a0 + P * A_BYTES;
+#pragma unroll
+          for (int k = 0; k < KSTEPS; ++k) {
+            const uint64_t ahi = ptx::desc_sw128(a0 + k * 32);
+            const uint64_t bhi = ptx::desc_sw128(b0 + k * 32);
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            if (SPLIT) {
+              const uint64_t alo = ptx::desc_sw128(a0 + A_BYTES + k * 32);
+              const uint64_t blo = ptx::desc_sw128(b0 + B_BYTES + k * 32);
+              ptx::mma<KIND>(d_tmem, ahi, blo, p.idesc, acc);
+              ptx::mma<KIND>(d_tmem, alo, bhi, p.idesc, 1u);
+              ptx::mma<KIND>(d_tmem, ahi, bhi, p.idesc, 1u);
+            } else {
+              ptx::mma<KIND>(d_tmem, ahi, bhi, p.idesc, acc);
+            }
+          }
+          ptx::mma_commit(&aux->empty[s]);  // stage free once these MMAs have read it
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&aux->tfull[buf]);  // accumulator complete
+        if (++buf == 2) {
+          buf = 0;
+          aph ^= 1u;
+        }
+      }
+      // All MMAs issued by this thread complete before TMEM is released.
+      ptx::mma_commit(&aux->drain);
+      volatile int never = 0;
+      ptx::wait_bounded(&aux->drain, 0u, &never, kWaitNs);
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 ----------------
+    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    DestList<float>& dl = aux->dl[warp - 2];
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int64_t tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x) {
+      int64_t leaf;
+      int tm, tn;
+      tile_coords(tile, p, &leaf, &tm, &tn);
+      __syncwarp();  // every lane is done with the previous tile's list
+      if (p.epi == 0 && lane == 0) build_dest_list(t, leaf, dl);
+      int ok = 1;
+      if (lane == 0) ok = ptx::wait_bounded(&aux->tfull[buf], aph, abort, kWaitNs) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) raise_abort(abort, p.status);
+        break;
+      }
+      __syncwarp();
+      ptx::tc_fence_after();
+      const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        ptx::tmem_ld32(tbase + (uint32_t)c0, v);
+        if (c0 + 32 == BN) {
+          // accumulator fully read: hand it back to the MMA warp before the global writes
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&aux->tempty[buf]);
+        }
+        const int64_t col0 = (int64_t)tn * BN + c0;
+        if (p.epi == 2) {
+          float* dst = p.M + leaf * p.strideM + row * p.ldm + col0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          continue;
+        }
+        if (row >= p.m) continue;
+        if (p.epi == 1) {
+          float* dst = p.C + row * p.ldc + col0;
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (col0 + q < p.m) dst[q] = v[q];
+          continue;
+        }
+        for (int d = 0; d < dl.total; ++d) {
+          int64_t I, J;
+          const float coef = dest_at(dl, d, t.n0, t.L, &I, &J);
+          float* dst = p.C + (I * p.m + row) * p.ldc + J * p.m + col0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int64_t c = col0 + 4 * q;
+            if (p.vec_ok && c + 3 < p.m) {
+              ptx::red_add_v4(dst + 4 * q, coef * v[4 * q], coef * v[4 * q + 1], coef * v[4 * q + 2],
+                              coef * v[4 * q + 3]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (c + e < p.m) atomicAdd(dst + 4 * q + e, coef * v[4 * q + e]);
+            }
+          }
+        }
+      }
+      if (++buf == 2) {
+        buf = 0;
+        aph ^= 1u;
+      }
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, 2 * BN);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+// 2D map over rows x K elements (row-major, K contiguous) with a box of box_rows x 128 bytes.
+bool make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int es, int64_t K, int64_t rows,
+              int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(K * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int KIND, int SPLIT, int BN, int STAGES>
+cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t, const Params& p,
+                   cudaStream_t st) {
+  constexpr int P = SPLIT ? 2 : 1;
+  constexpr size_t smem = (size_t)STAGES * P * (BM + BN) * kRowBytes + sizeof(Aux<STAGES>) + 1024;
+  static_assert(smem <= 232448, "shared memory budget");
+  auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES>;
+  const cudaError_t attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr_err != cudaSuccess) return attr_err;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = p.total_tiles < sms ? p.total_tiles : sms;
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(ma, mb, t, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
+bool tc_supports_store_m() { return true; }
+
+cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStream_t st) {
+  const bool tf32 = a.leaf == RBC_LEAF_TF32 || a.leaf == RBC_LEAF_3XTF32;
+  const bool split = a.leaf == RBC_LEAF_3XTF32 || a.leaf == RBC_LEAF_3XBF16;
+  const int es = tf32 ? 4 : 2;
+  const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (a.leaf == RBC_LEAF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const int bn = (!split && a.mp % 256 == 0) ? 256 : 128;
+  if (a.mp % 128 || a.mp % bn) return cudaErrorInvalidValue;
+  const int64_t rows = a.leaves * a.mp;
+  if (rows > INT32_MAX || a.K > INT32_MAX) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a.S, dt, es, a.K, rows, BM) || !make_map(&mb, a.Tt, dt, es, a.K, rows, bn))
+    return cudaErrorInvalidValue;
+  Params p{};
+  p.m = a.m;
+  p.mp = a.mp;
+  p.leaves = a.leaves;
+  p.tiles_m = (int)(a.mp / BM);
+  p.tiles_n = (int)(a.mp / bn);
+  p.total_tiles = a.leaves * p.tiles_m * p.tiles_n;
+  const int kelem = kRowBytes / es;
+  p.nk = (int)(a.mp / kelem);
+  p.kpanel = (int)a.mp;
+  const uint32_t fmt = tf32 ? 2u : (a.leaf == RBC_LEAF_F16 ? 0u : 1u);
+  p.idesc = ptx::idesc(fmt, fmt, BM, bn);
+  p.epi = a.store_m ? 2 : (a.direct ? 1 : 0);
+  p.C = static_cast<float*>(a.C);
+  p.ldc = a.ldc;
+  p.vec_ok = ((uintptr_t)a.C % 16 == 0) && a.ldc % 4 == 0 && a.m % 4 == 0;
+  p.M = static_cast<float*>(a.M);
+  p.ldm = a.mp;
+  p.strideM = a.mp * a.mp;
+  p.status = a.status;
+  if (tf32) {
+    if (split) return launch<1, 1, 128, 3>(ma, mb, t, p, st);
+    if (bn == 256) return launch<1, 0, 256, 4>(ma, mb, t, p, st);
+    return launch<1, 0, 128, 6>(ma, mb, t, p, st);
+  }
+  if (split) return launch<0, 1, 128, 3>(ma, mb, t, p, st);
+  if (bn == 256) return launch<0, 0, 256, 4>(ma, mb, t, p, st);
+  return launch<0, 0, 128, 6>(ma, mb, t, p, st);
+}
+
 }  // namespace rbc

@@ -120,3 +120,58 @@ def test_norms_match_numpy(rbc):
     assert np.isclose(out2[0], np.sum(X**2), rtol=1e-12) and out2[1] == 0.0
     # deterministic: repeated calls are bit-identical
     assert np.array_equal(rbc.norms(Xt, Yt).cpu().numpy(), out)
+
+
+TC_CASES = [
+    # formula, L, N: classical ragged, both tile widths (mp % 256 == 0 and != 0), n0 = 3, approximate
+    ("strassen", 0, 300),
+    ("strassen", 1, 2 * 200),
+    ("strassen", 2, 4 * 300),
+    ("strassen", 2, 4 * 512),
+    ("strassen", 3, 8 * 70),
+    ("laderman", 2, 9 * 100),
+    ("noisy-strassen", 2, 4 * 260),
+]
+
+
+@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32"])
+@pytest.mark.parametrize("decode", [1, 2])
+@pytest.mark.parametrize("name,L,N", TC_CASES)
+def test_tensor_core_leaves_match_oracle(rbc, name, L, N, decode, leaf):
+    U, V, W = formula(name, seed=3)
+    A, B = matrix_pair("normal", N, seed=30 + L)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    plan = rbc.Plan(U, V, W, levels=L, seed=555)
+    C = gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_NAMES[leaf], decode)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, 555))
+    err = normwise(C, ref, A, B)
+    assert err <= gate(leaf, U.shape[0], L, N), (err, gate(leaf, U.shape[0], L, N))
+
+
+def test_split_modes_are_fp32_accurate(rbc):
+    # The compensated modes must be far more accurate than their single-pass counterparts.
+    U, V, W = formula("strassen")
+    N, L = 1024, 2
+    A, B = matrix_pair("normal", N, seed=5)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    plan = rbc.Plan(U, V, W, levels=L, seed=1)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, 1))
+    errs = {leaf: rel(gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_NAMES[leaf]), ref)
+            for leaf in ("f32", "tf32", "3xtf32", "bf16", "3xbf16")}
+    assert errs["3xtf32"] < errs["tf32"] / 50
+    assert errs["3xbf16"] < errs["bf16"] / 50
+    assert errs["3xtf32"] < 4 * errs["f32"] + 1e-7
+
+
+def test_workspace_status_word_clear_after_calls(rbc):
+    import ctypes
+    U, V, W = formula("strassen")
+    plan = rbc.Plan(U, V, W, levels=1, seed=1)
+    A = torch.randn((512, 512), device="cuda")
+    ws = torch.empty(plan.workspace_size(512, rbc.IO_F32, rbc.LEAF_BF16), dtype=torch.uint8, device="cuda")
+    rbc.matmul(plan, A, A, leaf=rbc.LEAF_BF16, workspace=ws)
+    st = ctypes.c_int(-1)
+    rbc.rbc.check(rbc.lib().rbc_workspace_check(ws.data_ptr(), None, ctypes.byref(st)), "check")
+    assert st.value == 0
