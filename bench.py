@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--cases", default="all", help="'all' or comma list of indices into the sweep")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--decode", type=int, default=0, help="0 auto, 1 fused, 2 staged")
     return ap.parse_args()
 
 
@@ -157,7 +158,7 @@ def run_ours(args):
     for name, n, L in cases:
         U, V, W = formula_by_name(name, seed=7)
         plans.append(rbc.Plan(U, V, W, levels=L, seed=2024 + L))
-    ws_bytes = max(p.workspace_size(n, rbc.IO_F32, leaf) for p, (_, n, _) in zip(plans, cases))
+    ws_bytes = max(p.workspace_size(n, rbc.IO_F32, leaf, args.decode) for p, (_, n, _) in zip(plans, cases))
     if ws_bytes == 0:
         raise RuntimeError("invalid leaf mode for this workload")
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -172,7 +173,7 @@ def run_ours(args):
     def step(events=None, counts=None):
         for i, (plan, (name, n, L)) in enumerate(zip(plans, cases)):
             x = inputs[n]
-            o = rbc.rbc.rbc_matmul_opts(0)
+            o = rbc.rbc.rbc_matmul_opts(args.decode)
             if events is not None:
                 for j, e in enumerate(events[i]):
                     o.events[j] = e.cuda_event
@@ -227,6 +228,7 @@ def run_ours(args):
         g = statistics.mean(ev_sets[s][i][1].elapsed_time(ev_sets[s][i][2]) for s in range(args.steps))
         e = statistics.mean(ev_sets[s][i][0].elapsed_time(ev_sets[s][i][1]) for s in range(args.steps))
         tot = statistics.mean(ev_sets[s][i][0].elapsed_time(ev_sets[s][i][3]) for s in range(args.steps))
+        dec = statistics.mean(ev_sets[s][i][2].elapsed_time(ev_sets[s][i][3]) for s in range(args.steps))
         lf = split * 2.0 * R**L * m**3
         leaf_ms += g
         leaf_flops += lf
@@ -237,7 +239,8 @@ def run_ours(args):
         per_case.append({"formula": nm, "n": n, "L": L, "ms": round(tot, 3),
                          "eff_tflops": round(2.0 * n**3 / tot / 1e9, 2),
                          "leaf_ms": round(g, 3), "leaf_tflops": round(lf / g / 1e9, 2),
-                         "encode_ms": round(e, 3), "encode_gbs": round(eb / e / 1e6, 1)})
+                         "encode_ms": round(e, 3), "encode_gbs": round(eb / e / 1e6, 1),
+                         "decode_ms": round(dec, 3)})
     pk, pk_kind = peaks()
     if args.leaf in ("f32",):
         bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
@@ -263,7 +266,7 @@ def run_ours(args):
                 x = inputs[n]
                 x["A"].copy_(x["hA"], non_blocking=True)
                 x["B"].copy_(x["hB"], non_blocking=True)
-                rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws)
+                rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws, decode=args.decode)
                 x["hC"].copy_(x["C"], non_blocking=True)
         e2e_step()
         barrier()
@@ -294,7 +297,7 @@ def run_ours(args):
             del A64, B64
         for plan, (nm, n, L) in zip(plans, cases):
             x = inputs[n]
-            rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws)
+            rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws, decode=args.decode)
             nr = rbc.norms(x["C"], truths[n]).cpu().numpy()
             errors.append({"formula": nm, "n": n, "L": L, "rel_fro_vs_fp64_ab": float(np.sqrt(nr[0] / nr[1]))})
         torch.cuda.synchronize(dev)

@@ -30,8 +30,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     simt_gemm_kernel(const __grid_constant__ Tables<T> t, const SimtGemmArgs a) {
   constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
   constexpr int EA = BM * BK / NT, EB = BN * BK / NT;
-  static_assert(BK % EA == 0 && BK % EB == 0, "tile/thread mismatch");
-  constexpr int KA = BK / EA, KB = BK / EB;  // threads per tile row
+  static_assert(BK % EA == 0 && BN % EB == 0 && (BN / EB) * BK == NT, "tile/thread mismatch");
+  constexpr int KA = BK / EA;   // threads per row of the S tile (BM rows x BK)
+  constexpr int KB = BN / EB;   // threads per row of the T tile (BK rows x BN)
   __shared__ T As[2][BK][BM];
   __shared__ T Bs[2][BK][BN];
   __shared__ DestList<T> dl;
@@ -40,12 +41,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tx = tid % TX, ty = tid / TX;
   const int64_t row0 = (int64_t)blockIdx.y * BM, col0 = (int64_t)blockIdx.x * BN;
   const int ar = tid / KA, ak = (tid % KA) * EA;
-  const int br = tid / KB, bk = (tid % KB) * EB;
+  const int bk = tid / KB, bn = (tid % KB) * EB;
   const int nk = (int)(a.K / BK);
 
   for (int64_t leaf = blockIdx.z; leaf < a.leaves; leaf += gridDim.z) {
     const T* S = static_cast<const T*>(a.S) + leaf * a.strideS + (row0 + ar) * a.lds + ak;
-    const T* Tt = static_cast<const T*>(a.Tt) + leaf * a.strideT + (col0 + br) * a.ldt + bk;
+    const T* Tp = static_cast<const T*>(a.T) + leaf * a.strideT + (int64_t)bk * a.ldt + col0 + bn;
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -54,18 +55,18 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 
     T ra[EA], rb[EB];
     load_vec<T, EA>(ra, S);
-    load_vec<T, EB>(rb, Tt);
+    load_vec<T, EB>(rb, Tp);
     __syncthreads();  // previous leaf's readers are done with buffer 0
 #pragma unroll
     for (int e = 0; e < EA; ++e) As[0][ak + e][ar] = ra[e];
 #pragma unroll
-    for (int e = 0; e < EB; ++e) Bs[0][bk + e][br] = rb[e];
+    for (int e = 0; e < EB; ++e) Bs[0][bk][bn + e] = rb[e];
     __syncthreads();
     for (int kt = 0; kt < nk; ++kt) {
       const int buf = kt & 1;
       if (kt + 1 < nk) {
         load_vec<T, EA>(ra, S + (int64_t)(kt + 1) * BK);
-        load_vec<T, EB>(rb, Tt + (int64_t)(kt + 1) * BK);
+        load_vec<T, EB>(rb, Tp + (int64_t)(kt + 1) * BK * a.ldt);
       }
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
         for (int e = 0; e < EA; ++e) As[buf ^ 1][ak + e][ar] = ra[e];
 #pragma unroll
-        for (int e = 0; e < EB; ++e) Bs[buf ^ 1][bk + e][br] = rb[e];
+        for (int e = 0; e < EB; ++e) Bs[buf ^ 1][bk][bn + e] = rb[e];
       }
       __syncthreads();
     }

@@ -7,43 +7,46 @@
 
 namespace rbc {
 
-struct EncodeArgs {
-  const void* X;        // parents: parent p at X + p*strideX, leading dim ldx (elements)
+// One encode or decode pass over G consecutive levels (parents at depth `depth`).
+//   encode: X = parents (parent p at X + p*strideX, leading dim ldx), each an n0^G x n0^G grid
+//           of nb x nb blocks; Y = outputs, output `path` of parent p at
+//           Y + (p*outs_per_parent + path)*strideY, leading dim ldy, rows_out x cols_out written
+//           (entries beyond nb are zero padding), split panels [hi | lo] kpanel apart.
+//   decode: X = children (child `path` of parent p at X + (p*outs_per_parent + path)*strideX,
+//           leading dim ldx, nb x nb valid); Y = parents (p*strideY, leading dim ldy).
+// Draw set of a node at relative depth j with heap id n: draw[dbase[j] + n - dfirst[j]]
+// (per-node scope) or draw[depth + j] (per-level scope).
+struct PassArgs {
+  const void* X;
   int64_t ldx, strideX;
-  void* Y;              // children: child p*R + r at Y + (p*R + r)*strideY, leading dim ldy
+  void* Y;
   int64_t ldy, strideY;
-  int64_t nb;           // child block size (valid rows = cols)
-  int64_t rows_out;     // written output rows (>= nb; rows beyond nb are zero padding)
-  int64_t cols_out;     // written output columns per panel (>= nb)
-  int64_t parents;      // number of parent nodes in this launch
-  int64_t node_first;   // heap id of parent 0
-  int tensor;           // 0: left operand (u^), 1: right operand (v^)
-  int trans;            // 1: write each child transposed
-  int split;            // 0: plain; 1: split panels [hi | lo] (hi = round(x), lo = round(x - hi))
-  int64_t kpanel;       // column offset between split panels
-};
-
-struct DecodeArgs {
-  const void* M;        // children: child p*R + r at M + (p*R + r)*strideM, leading dim ldm
-  int64_t ldm, strideM;
-  void* P;              // parents: parent p at P + p*strideP, leading dim ldp
-  int64_t ldp, strideP;
-  int64_t nb;           // child block size
+  int64_t nb;
+  int64_t rows_out, cols_out;
   int64_t parents;
+  int64_t outs_per_parent;
   int64_t node_first;
+  int depth;
+  int tensor;     // encode: 0 left operand (u^), 1 right operand (v^)
+  int split;      // encode: write [hi | lo] panels
+  int64_t kpanel;
+  int64_t dbase[kMaxLevels];
+  int64_t dfirst[kMaxLevels];
 };
 
-cudaError_t launch_encode_level(const Tables<double>& t, const EncodeArgs& a, int n0, int io,
-                                int store, cudaStream_t st);
-cudaError_t launch_encode_level(const Tables<float>& t, const EncodeArgs& a, int n0, int io,
-                                int store, cudaStream_t st);
-cudaError_t launch_decode_level(const Tables<double>& t, const DecodeArgs& a, int n0, cudaStream_t st);
-cudaError_t launch_decode_level(const Tables<float>& t, const DecodeArgs& a, int n0, cudaStream_t st);
+int max_levels_per_pass(int n0);
+// g = 0 is the identity pass of L = 0 (conversion and padding of the single leaf).
+cudaError_t launch_encode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, int io, int store,
+                               cudaStream_t st);
+cudaError_t launch_encode_pass(const Tables<float>& t, const PassArgs& a, int n0, int g, int io, int store,
+                               cudaStream_t st);
+cudaError_t launch_decode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, cudaStream_t st);
+cudaError_t launch_decode_pass(const Tables<float>& t, const PassArgs& a, int n0, int g, cudaStream_t st);
 
-// Batched leaf products M_leaf = S_leaf * T_leaf^T on the CUDA cores (fp32 or fp64 FMA).
+// Batched leaf products M_leaf = S_leaf * T_leaf on the CUDA cores (fp32 or fp64 FMA).
 struct SimtGemmArgs {
   const void* S;        // left operands [leaf][mp][K] row-major, leading dim lds
-  const void* Tt;       // right operands stored transposed [leaf][mp][K], leading dim ldt
+  const void* T;        // right operands [leaf][mp (k)][row length ldt >= mp (n)] row-major
   int64_t lds, ldt, strideS, strideT;
   int64_t K;            // inner dimension (multiple of the tile K)
   int64_t m;            // valid rows/cols of each leaf product

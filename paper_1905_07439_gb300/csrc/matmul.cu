@@ -41,14 +41,48 @@ int leaf_store(int leaf) {
 
 size_t store_bytes(int s) { return s == kStoreF64 ? 8 : (s == kStoreBF16 || s == kStoreF16) ? 2 : 4; }
 
+// Grouping of the L levels into passes, root first: [L - (k-1)*g, g, ..., g] with g the most
+// levels one pass holds in registers; the small pass sits at the root, where intermediates
+// are smallest ((R/n0^2)^depth N^2 elements).
+struct Passes {
+  int count = 0;
+  int g[kMaxLevels] = {};
+  int top[kMaxLevels] = {};  // depth of the parents of each pass
+};
+
+Passes plan_passes(int L, int n0) {
+  Passes ps;
+  if (L == 0) return ps;
+  const int g = max_levels_per_pass(n0);
+  const int k = (L + g - 1) / g;
+  int depth = 0;
+  for (int i = 0; i < k; ++i) {
+    ps.g[i] = i == 0 ? L - (k - 1) * g : g;
+    ps.top[i] = depth;
+    depth += ps.g[i];
+  }
+  ps.count = k;
+  return ps;
+}
+
 struct Layout {
   int64_t m = 0, mp = 0, K = 0;
-  int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 level by level
+  int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 staged passes
   size_t es_io = 0, es_acc = 0, es_leaf = 0;
-  size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};
+  Passes passes;
+  size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
   size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
   size_t total = 0;
 };
+
+// Contributions per C element of the fused decode: (sum_r nnz(W_::r) / n0^2)^L.
+double fused_contributions(const rbc_plan_s* p) {
+  int nnz = 0;
+  for (double w : p->W) nnz += w != 0.0;
+  double per = (double)nnz / (p->n0 * p->n0), c = 1.0;
+  for (int d = 0; d < p->L; ++d) c *= per;
+  return c;
+}
 
 rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo) {
   if (!p) return fail(RBC_EINVAL, "null plan");
@@ -61,6 +95,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   const int64_t blocks = ipow(p->n0, p->L);
   if (N <= 0 || N % blocks) return fail(RBC_EINVAL, "N must be a positive multiple of n0^L");
   const int L = p->L, R = p->R, n0 = p->n0;
+  if (n0 * n0 * R > kMaxCoef) return fail(RBC_EUNSUPPORTED, "n0*n0*R exceeds the kernel table size (256)");
   lo->m = N / blocks;
   lo->es_io = io == RBC_IO_F64 ? 8 : 4;
   lo->es_acc = lo->es_io;
@@ -74,13 +109,21 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     lo->mp = (lo->m + tile - 1) / tile * tile;
   }
   lo->K = lo->mp * (lo->split ? 2 : 1);
+  lo->passes = plan_passes(L, n0);
   const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;
-  lo->decode = decode_req == 2 || !fused_ok ? 2 : 1;
   if (decode_req == 1 && !fused_ok) return fail(RBC_EUNSUPPORTED, "fused decode needs <= 1024 draw sets");
-  if (lo->decode == 2 && is_tc_leaf(leaf) && !tc_supports_store_m())
-    return fail(RBC_EUNSUPPORTED, "level-by-level decode is not available for tensor-core leaves");
+  if (decode_req == 0) {
+    // Fused scatter costs one read-modify-write of C per contribution; it pays only when C
+    // stays in L2 and few leaves feed each element.
+    const double c_bytes = (double)N * N * lo->es_io;
+    lo->decode = (fused_ok && L <= 1 && c_bytes <= 64.0 * (1 << 20) && fused_contributions(p) <= 4.0) ? 1 : 2;
+  } else {
+    lo->decode = decode_req;
+  }
+  if (L == 0) lo->decode = 1;
   size_t off = kStatusBytes;  // device status word(s) first
-  for (int d = 1; d < L; ++d) {
+  for (int i = 1; i < lo->passes.count; ++i) {
+    const int d = lo->passes.top[i];
     const int64_t nd = lo->m * ipow(n0, L - d);
     const size_t bytes = align256((size_t)ipow(R, d) * nd * nd * lo->es_io);
     lo->encA[d] = off;
@@ -97,7 +140,8 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   if (lo->decode == 2 && L > 0) {
     lo->M = off;
     off += align256((size_t)leaves * lo->mp * lo->mp * lo->es_acc);
-    for (int d = 1; d < L; ++d) {
+    for (int i = 1; i < lo->passes.count; ++i) {
+      const int d = lo->passes.top[i];
       const int64_t nd = lo->m * ipow(n0, L - d);
       lo->dec[d] = off;
       off += align256((size_t)ipow(R, d) * nd * nd * lo->es_acc);
@@ -112,46 +156,69 @@ struct TablesBox {
   std::unique_ptr<Tables<T>> t{new Tables<T>()};
 };
 
-// Encode one operand through all levels into the leaf operand buffer.
+// Load the draw sets of parents [c0, c0 + cnt) at depth d and their subtrees over g levels.
+template <typename T>
+rbc_status pass_tables(const rbc_plan_s* p, int d, int g, int64_t c0, int64_t cnt, PassArgs* a, Tables<T>& tab) {
+  a->depth = d;
+  a->node_first = depth_start(p->R, d) + c0;
+  if (p->scope == RBC_DRAW_PER_LEVEL) return fill_tables(p, 0, p->draw_count, &tab);
+  int64_t first[kMaxLevels], count[kMaxLevels], base = 0;
+  for (int j = 0; j < g; ++j) {
+    const int64_t rj = ipow(p->R, j);
+    first[j] = depth_start(p->R, d + j) + c0 * rj;
+    count[j] = cnt * rj;
+    a->dfirst[j] = first[j];
+    a->dbase[j] = base;
+    base += count[j];
+  }
+  return fill_tables_ranges(p, first, count, g, &tab);
+}
+
+// Parents per launch so that the subtree draws of a chunk fit the kernel table.
+int64_t pass_chunk(const rbc_plan_s* p, int g, int64_t parents) {
+  if (p->scope == RBC_DRAW_PER_LEVEL) return parents;
+  int64_t per = 0;
+  for (int j = 0; j < g; ++j) per += ipow(p->R, j);
+  const int64_t c = kMaxDraws / per;
+  return c < 1 ? 1 : c;
+}
+
+// Encode one operand through all passes into the leaf operand buffer (row-major, K-major
+// rows of length lo.K, zero padded to mp, split panels [hi | lo]).
 template <typename T>
 rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
                           int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st) {
   const int L = p->L, R = p->R, n0 = p->n0;
   const size_t* enc = tensor == 0 ? lo.encA : lo.encB;
   char* leafbuf = ws + (tensor == 0 ? lo.leafS : lo.leafT);
-  if (L == 0) {  // identity "encode": conversion, padding, layout of the single leaf
-    rbc_status s = fill_tables(p, 0, 0, &tab);
-    if (s != RBC_OK) return s;
-    EncodeArgs a{};
+  if (L == 0) {
+    PassArgs a{};
     a.X = X;
     a.ldx = ldx;
     a.Y = leafbuf;
     a.ldy = lo.K;
-    a.strideY = lo.mp * lo.K;
     a.nb = lo.m;
     a.rows_out = lo.mp;
     a.cols_out = lo.mp;
     a.parents = 1;
-    a.tensor = tensor;
-    a.trans = tensor == 1;
+    a.outs_per_parent = 1;
     a.split = lo.split;
     a.kpanel = lo.mp;
-    cudaError_t e = launch_encode_level(tab, a, 1, io, lo.store, st);
+    cudaError_t e = launch_encode_pass(tab, a, n0, 0, io, lo.store, st);
     ++g_launches;
     return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
   }
-  for (int d = 0; d < L; ++d) {
-    const int64_t n_par = lo.m * ipow(n0, L - d), nb = n_par / n0;
-    const int64_t parents = ipow(R, d);
-    const bool last = d == L - 1;
-    const int64_t chunk = p->scope == RBC_DRAW_PER_LEVEL ? parents : kMaxDraws;
+  for (int i = 0; i < lo.passes.count; ++i) {
+    const int d = lo.passes.top[i], g = lo.passes.g[i];
+    const bool last = i + 1 == lo.passes.count;
+    const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
+    const int64_t parents = ipow(R, d), outs = ipow(R, g);
+    const int64_t chunk = pass_chunk(p, g, parents);
     for (int64_t c0 = 0; c0 < parents; c0 += chunk) {
       const int64_t cnt = std::min(chunk, parents - c0);
-      const int64_t node_first = depth_start(R, d) + c0;
-      rbc_status s = p->scope == RBC_DRAW_PER_LEVEL ? fill_tables(p, d, 1, &tab)
-                                                    : fill_tables(p, node_first, cnt, &tab);
+      PassArgs a{};
+      rbc_status s = pass_tables(p, d, g, c0, cnt, &a, tab);
       if (s != RBC_OK) return s;
-      EncodeArgs a{};
       if (d == 0) {
         a.X = X;
         a.ldx = ldx;
@@ -162,16 +229,15 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
         a.strideX = n_par * n_par;
       }
       if (last) {
-        a.Y = leafbuf + (size_t)c0 * R * lo.mp * lo.K * lo.es_leaf;
+        a.Y = leafbuf + (size_t)c0 * outs * lo.mp * lo.K * lo.es_leaf;
         a.ldy = lo.K;
         a.strideY = lo.mp * lo.K;
         a.rows_out = lo.mp;
         a.cols_out = lo.mp;
-        a.trans = tensor == 1;
         a.split = lo.split;
         a.kpanel = lo.mp;
       } else {
-        a.Y = ws + enc[d + 1] + (size_t)c0 * R * nb * nb * lo.es_io;
+        a.Y = ws + enc[d + g] + (size_t)c0 * outs * nb * nb * lo.es_io;
         a.ldy = nb;
         a.strideY = nb * nb;
         a.rows_out = nb;
@@ -179,10 +245,10 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
       }
       a.nb = nb;
       a.parents = cnt;
-      a.node_first = node_first;
+      a.outs_per_parent = outs;
       a.tensor = tensor;
       const int store = last ? lo.store : (io == RBC_IO_F64 ? kStoreF64 : kStoreF32);
-      cudaError_t e = launch_encode_level(tab, a, n0, io, store, st);
+      cudaError_t e = launch_encode_pass(tab, a, n0, g, io, store, st);
       ++g_launches;
       if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
     }
@@ -190,43 +256,44 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
   return RBC_OK;
 }
 
+// Staged decode: passes from the leaves up to C.
 template <typename T>
-rbc_status decode_levels(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
+rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
                          Tables<T>& tab, cudaStream_t st) {
   const int L = p->L, R = p->R, n0 = p->n0;
-  for (int d = L - 1; d >= 0; --d) {
-    const int64_t n_par = lo.m * ipow(n0, L - d), nb = n_par / n0;
-    const int64_t parents = ipow(R, d);
-    const int64_t chunk = p->scope == RBC_DRAW_PER_LEVEL ? parents : kMaxDraws;
+  for (int i = lo.passes.count - 1; i >= 0; --i) {
+    const int d = lo.passes.top[i], g = lo.passes.g[i];
+    const bool bottom = i + 1 == lo.passes.count;
+    const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
+    const int64_t parents = ipow(R, d), outs = ipow(R, g);
+    const int64_t chunk = pass_chunk(p, g, parents);
     for (int64_t c0 = 0; c0 < parents; c0 += chunk) {
       const int64_t cnt = std::min(chunk, parents - c0);
-      const int64_t node_first = depth_start(R, d) + c0;
-      rbc_status s = p->scope == RBC_DRAW_PER_LEVEL ? fill_tables(p, d, 1, &tab)
-                                                    : fill_tables(p, node_first, cnt, &tab);
+      PassArgs a{};
+      rbc_status s = pass_tables(p, d, g, c0, cnt, &a, tab);
       if (s != RBC_OK) return s;
-      DecodeArgs a{};
-      if (d + 1 == L) {
-        a.M = ws + lo.M + (size_t)c0 * R * lo.mp * lo.mp * lo.es_acc;
-        a.ldm = lo.mp;
-        a.strideM = lo.mp * lo.mp;
+      if (bottom) {
+        a.X = ws + lo.M + (size_t)c0 * outs * lo.mp * lo.mp * lo.es_acc;
+        a.ldx = lo.mp;
+        a.strideX = lo.mp * lo.mp;
       } else {
-        a.M = ws + lo.dec[d + 1] + (size_t)c0 * R * nb * nb * lo.es_acc;
-        a.ldm = nb;
-        a.strideM = nb * nb;
+        a.X = ws + lo.dec[d + g] + (size_t)c0 * outs * nb * nb * lo.es_acc;
+        a.ldx = nb;
+        a.strideX = nb * nb;
       }
       if (d == 0) {
-        a.P = C;
-        a.ldp = ldc;
-        a.strideP = 0;
+        a.Y = C;
+        a.ldy = ldc;
+        a.strideY = 0;
       } else {
-        a.P = ws + lo.dec[d] + (size_t)c0 * n_par * n_par * lo.es_acc;
-        a.ldp = n_par;
-        a.strideP = n_par * n_par;
+        a.Y = ws + lo.dec[d] + (size_t)c0 * n_par * n_par * lo.es_acc;
+        a.ldy = n_par;
+        a.strideY = n_par * n_par;
       }
       a.nb = nb;
       a.parents = cnt;
-      a.node_first = node_first;
-      cudaError_t e = launch_decode_level(tab, a, n0, st);
+      a.outs_per_parent = outs;
+      cudaError_t e = launch_decode_pass(tab, a, n0, g, st);
       ++g_launches;
       if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
     }
@@ -267,7 +334,7 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
   if (is_tc_leaf(leaf)) {
     TcGemmArgs g{};
     g.S = ws + lo.leafS;
-    g.Tt = ws + lo.leafT;
+    g.T = ws + lo.leafT;
     g.K = lo.K;
     g.m = lo.m;
     g.mp = lo.mp;
@@ -289,7 +356,7 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
   } else {
     SimtGemmArgs g{};
     g.S = ws + lo.leafS;
-    g.Tt = ws + lo.leafT;
+    g.T = ws + lo.leafT;
     g.lds = lo.K;
     g.ldt = lo.K;
     g.strideS = lo.mp * lo.K;
@@ -314,7 +381,7 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
   }
   mark(opts, 2, st);
   if (!fused) {
-    s = decode_levels<T>(p, lo, C, ldc, ws, tab, st);
+    s = decode_passes<T>(p, lo, C, ldc, ws, tab, st);
     if (s != RBC_OK) return s;
   }
   mark(opts, 3, st);

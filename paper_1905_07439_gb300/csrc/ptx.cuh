@@ -156,9 +156,24 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: fp32 accumulator, operand formats, K-major A and B, N and M.
-__host__ __device__ constexpr uint32_t idesc(uint32_t a_fmt, uint32_t b_fmt, uint32_t M, uint32_t N) {
-  return (1u << 4) | (a_fmt << 7) | (b_fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+// Descriptor of an MN-major tile with the 128-byte swizzle: atoms of 128 bytes along MN x 8
+// rows along K (1024 bytes); `lbo` = byte stride between atoms along MN, stride-dimension
+// byte offset 1024 = between 8-row groups along K.
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: fp32 accumulator, operand formats, A K-major, B K-major (b_mn = 0)
+// or MN-major (b_mn = 1), N and M.
+__host__ __device__ constexpr uint32_t idesc(uint32_t a_fmt, uint32_t b_fmt, uint32_t M, uint32_t N,
+                                             uint32_t b_mn = 0) {
+  return (1u << 4) | (a_fmt << 7) | (b_fmt << 10) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {

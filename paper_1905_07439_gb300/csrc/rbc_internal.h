@@ -86,5 +86,9 @@ inline int64_t ipow(int64_t b, int e) {
 // Fill the tables of a launch touching draw sets [key_first, key_first + count).
 template <typename T>
 rbc_status fill_tables(const rbc_plan_s* p, int64_t key_first, int64_t count, Tables<T>* t);
+// Same with the concatenation of several ranges [first[i], first[i] + count[i]).
+template <typename T>
+rbc_status fill_tables_ranges(const rbc_plan_s* p, const int64_t* first, const int64_t* count, int nranges,
+                              Tables<T>* t);
 
 }  // namespace rbc

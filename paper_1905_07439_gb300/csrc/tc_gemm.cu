@@ -3,8 +3,9 @@
 // Eq. recursive-random-formula fused into the epilogue.
 //
 // Persistent, warp-specialized kernel, one CTA per SM (192 threads):
-//   warp 0     one thread issues TMA loads of the K-major S and T^T tiles (128-byte swizzle)
-//              into a ring of shared-memory stages (mbarrier full/empty handshake);
+//   warp 0     one thread issues TMA loads of the S tile (K-major) and the T tile (MN-major:
+//              T is stored row-major with n contiguous) with the 128-byte swizzle into a ring
+//              of shared-memory stages (mbarrier full/empty handshake);
 //   warp 1     allocates TMEM (two fp32 accumulators of 128 x BN) and one thread issues
 //              tcgen05.mma (M = 128, N = BN, K = 16 bf16/f16 or 8 tf32 per instruction),
 //              committing stage releases and accumulator-ready signals;
@@ -80,8 +81,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int P = SPLIT ? 2 : 1;
   constexpr uint32_t A_BYTES = BM * kRowBytes, B_BYTES = BN * kRowBytes;
   constexpr uint32_t STAGE_BYTES = P * (A_BYTES + B_BYTES);
-  constexpr int KSTEPS = kRowBytes / 32;  // MMA K steps of 32 bytes per stage
-  constexpr int KELEM = KIND == 0 ? 64 : 32;
+  constexpr int KSTEPS = kRowBytes / 32;  // MMA K steps per stage (32 bytes of K in A rows)
+  constexpr int KELEM = KIND == 0 ? 64 : 32;   // K elements per stage
+  constexpr int KINSTR = KIND == 0 ? 16 : 8;   // K elements per MMA instruction
+  constexpr uint32_t B_ATOM = KELEM * 128;     // one MN atom column of B: KELEM rows x 128 B
+  constexpr int B_BOXES = BN / (kRowBytes / (KIND == 0 ? 2 : 4));
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int tm, tn;
         tile_coords(tile, p, &leaf, &tm, &tn);
         const int32_t rowA = (int32_t)(leaf * p.mp + (int64_t)tm * BM);
-        const int32_t rowB = (int32_t)(leaf * p.mp + (int64_t)tn * BN);
+        const int32_t colB = tn * BN;
         for (int kb = 0; kb < p.nk; ++kb) {
           if (!ptx::wait_bounded(&aux->empty[s], ph ^ 1u, abort, kWaitNs)) {
             raise_abort(abort, p.status);
@@ -135,8 +139,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int32_t kx = kb * KELEM;
           ptx::tma_load_2d(st, &tmA, &aux->full[s], kx, rowA);
           if (SPLIT) ptx::tma_load_2d(st + A_BYTES, &tmA, &aux->full[s], kx + p.kpanel, rowA);
-          ptx::tma_load_2d(st + P * A_BYTES, &tmB, &aux->full[s], kx, rowB);
-          if (SPLIT) ptx::tma_load_2d(st + P * A_BYTES + B_BYTES, &tmB, &aux->full[s], kx + p.kpanel, rowB);
+          const int32_t rowB = (int32_t)(leaf * p.mp) + kx;
+          constexpr int NBOX = kRowBytes / (KIND == 0 ? 2 : 4);
+#pragma unroll
+          for (int j = 0; j < B_BOXES; ++j) {
+            ptx::tma_load_2d(st + P * A_BYTES + j * B_ATOM, &tmB, &aux->full[s], colB + j * NBOX, rowB);
+            if (SPLIT)
+              ptx::tma_load_2d(st + P * A_BYTES + B_BYTES + j * B_ATOM, &tmB, &aux->full[s],
+                               colB + j * NBOX + p.kpanel, rowB);
+          }
           armed |= 1u << s;
           last_par = (last_par & ~(1u << s)) | (ph << s);
           if (++s == STAGES) {
@@ -177,11 +188,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < KSTEPS; ++k) {
             const uint64_t ahi = ptx::desc_sw128(a0 + k * 32);
-            const uint64_t bhi = ptx::desc_sw128(b0 + k * 32);
+            const uint64_t bhi = ptx::desc_sw128_mn(b0 + k * KINSTR * 128, B_ATOM);
             const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
             if (SPLIT) {
               const uint64_t alo = ptx::desc_sw128(a0 + A_BYTES + k * 32);
-              const uint64_t blo = ptx::desc_sw128(b0 + B_BYTES + k * 32);
+              const uint64_t blo = ptx::desc_sw128_mn(b0 + B_BYTES + k * KINSTR * 128, B_ATOM);
               ptx::mma<KIND>(d_tmem, ahi, blo, p.idesc, acc);
               ptx::mma<KIND>(d_tmem, alo, bhi, p.idesc, 1u);
               ptx::mma<KIND>(d_tmem, ahi, bhi, p.idesc, 1u);
@@ -350,7 +361,9 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   const int64_t rows = a.leaves * a.mp;
   if (rows > INT32_MAX || a.K > INT32_MAX) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, a.S, dt, es, a.K, rows, BM) || !make_map(&mb, a.Tt, dt, es, a.K, rows, bn))
+  // A: rows of S (K contiguous), boxes 128 rows x 128 B.  B: rows of T are k, n contiguous;
+  // boxes of (K elements per stage) rows x 128 B of n.
+  if (!make_map(&ma, a.S, dt, es, a.K, rows, BM) || !make_map(&mb, a.T, dt, es, a.K, rows, kRowBytes / es))
     return cudaErrorInvalidValue;
   Params p{};
   p.m = a.m;
@@ -363,7 +376,7 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   p.nk = (int)(a.mp / kelem);
   p.kpanel = (int)a.mp;
   const uint32_t fmt = tf32 ? 2u : (a.leaf == RBC_LEAF_F16 ? 0u : 1u);
-  p.idesc = ptx::idesc(fmt, fmt, BM, bn);
+  p.idesc = ptx::idesc(fmt, fmt, BM, bn, 1u);
   p.epi = a.store_m ? 2 : (a.direct ? 1 : 0);
   p.C = static_cast<float*>(a.C);
   p.ldc = a.ldc;

@@ -10,7 +10,7 @@ namespace rbc {
 
 struct TcGemmArgs {
   const void* S;   // left operands [leaf][mp][K], K-major, leaf storage type ([hi | lo] when split)
-  const void* Tt;  // right operands stored transposed [leaf][mp][K], K-major
+  const void* T;   // right operands [leaf][mp (k rows)][K (n, row length)], n contiguous
   int64_t K;       // row length of S and T^T (mp, or 2*mp for the split modes)
   int64_t m;       // valid rows/cols of each leaf product
   int64_t mp;      // padded rows/cols (multiple of the tile)

@@ -44,6 +44,7 @@ CASES_F64 = [
     ("strassen", 2, 148, o.RAND_FULL, o.DRAW_PER_LEVEL),
     ("strassen", 3, 88, o.RAND_SIGN, o.DRAW_PER_NODE),
     ("strassen", 4, 16 * 9, o.RAND_PERM, o.DRAW_PER_NODE),
+    ("strassen", 5, 32 * 3, o.RAND_FULL, o.DRAW_PER_NODE),      # 2801 draw sets: chunked passes
     ("strassen", 2, 4, o.RAND_FULL, o.DRAW_PER_NODE),          # m = 1
     ("laderman", 1, 3 * 70, o.RAND_FULL, o.DRAW_PER_NODE),
     ("laderman", 2, 9 * 13, o.RAND_FULL, o.DRAW_PER_NODE),
