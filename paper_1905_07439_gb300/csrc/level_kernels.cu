@@ -2,18 +2,25 @@
 // each pass covering G consecutive levels (G <= 3 for n0 = 2, G <= 2 for n0 = 3, G = 1 for
 // n0 = 4) so that the intermediate operands of those levels never leave registers.
 //
-// Encode pass: one thread owns one position (y, x) of the output blocks.  It reads the
-// n0^G x n0^G entries of its parent at that position, then walks the G-level subtree depth
-// first: at a node, child r receives S_r = sum_{k,l} u^(node)_{klr} X[k, l] (sub-blocks of the
-// node's input, l inner, k outer), and the leaves of the walk are written to the R^G output
-// operands.  u^ is formed in-kernel from the base tensor and the node's packed draw, both in
-// the constant bank (Prop. 10), so the randomization moves no data.
+// At the start of every parent, the CTA expands the randomized tables of the parent's
+// G-level subtree (Prop. 10: u^_klr = u_{pi1(k) pi2(l) r} s1(k) s2(l), likewise v^, w^) from
+// the base tensors and the nodes' packed draws, both held in the constant bank, into shared
+// memory.  The randomization therefore moves no operand data, and the inner loops read each
+// coefficient with one broadcast shared load.
+//
+// Encode pass: a thread owns VEC adjacent positions (y, x..x+VEC-1) of the output blocks. It
+// reads the n0^G x n0^G entries of its parent at those positions, then walks the subtree
+// depth first: at a node, child r receives S_r = sum_{k,l} u^(node)_{klr} X[k, l] (sub-blocks
+// of the node's input, l inner, k outer), and the leaves of the walk are the R^G outputs.
 //
 // Decode pass: the same walk in post-order.  A node's output block (i, j) is
-// sum_r w^(node)_{ijr} M_r (r sequential), M_r the child's output at this position.
+// sum_r w^(node)_{ijr} M_r (r sequential), M_r the child's output at these positions; the
+// children of a bottom node are loaded eight at a time so that their loads overlap.
 //
-// Neighbouring threads own neighbouring x, so every load and store is coalesced.
+// Neighbouring threads own neighbouring positions: every load and store is coalesced.
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include "convert.cuh"
 #include "level_kernels.cuh"
@@ -27,209 +34,443 @@ constexpr int kThreadsX = 128;
 
 __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 
-template <typename Tc>
-__device__ __forceinline__ uint64_t node_draw(const Tables<Tc>& t, const PassArgs& a, int rel_depth,
-                                              int64_t node) {
-  if (t.per_level) return t.draw[a.depth + rel_depth];
-  return t.draw[a.dbase[rel_depth] + (node - a.dfirst[rel_depth])];
+// Positions per thread when the layout allows vector access: keeps the per-thread working
+// set (about VEC * 1.33 * n0^(2G) values) within the register file.
+template <typename Tc, int N0, int G>
+struct Vec {
+  static constexpr int n = cpow(N0, 2 * G);
+  static constexpr int value = sizeof(Tc) == 8 ? (n >= 64 ? 1 : (n >= 16 ? 2 : 4)) : (n >= 64 ? 2 : 4);
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(T (&dst)[VEC], const T* src) {
+  if constexpr (VEC * sizeof(T) == 16) {
+    const int4 r = *reinterpret_cast<const int4*>(src);
+    memcpy(dst, &r, 16);
+  } else if constexpr (VEC * sizeof(T) == 8) {
+    const int2 r = *reinterpret_cast<const int2*>(src);
+    memcpy(dst, &r, 8);
+  } else {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) dst[v] = src[v];
+  }
 }
 
-__device__ __forceinline__ int64_t heap_child(int64_t node, int r, int R) { return node * R + r + 1; }
+template <typename T, int VEC>
+__device__ __forceinline__ void store_vec(T* dst, const T (&x)[VEC]) {
+  if constexpr (VEC * sizeof(T) == 16) {
+    int4 r;
+    memcpy(&r, x, 16);
+    *reinterpret_cast<int4*>(dst) = r;
+  } else if constexpr (VEC * sizeof(T) == 8) {
+    int2 r;
+    memcpy(&r, x, 8);
+    *reinterpret_cast<int2*>(dst) = r;
+  } else if constexpr (VEC * sizeof(T) == 4) {
+    int r;
+    memcpy(&r, x, 4);
+    *reinterpret_cast<int*>(dst) = r;
+  } else {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) dst[v] = x[v];
+  }
+}
+
+// Number of nodes of a G-level subtree with R children per node: sum_{j<G} R^j.
+__host__ __device__ inline int subtree_nodes(int R, int G) {
+  int s = 0, p = 1;
+  for (int j = 0; j < G; ++j) {
+    s += p;
+    p *= R;
+  }
+  return s;
+}
+// Local id of the node at relative depth j with path prefix q: sum_{i<j} R^i + q.
+__device__ __forceinline__ int local_id(int R, int j, int q) { return subtree_nodes(R, j) + q; }
+
+// Expand the tables of the G-level subtree under parent heap id hp (at depth a.depth) into
+// coef[(local * R + r) * n0^2 + a * n0 + b] for tensor `which` (0 u^, 1 v^, 2 w^).
+template <typename Tc>
+__device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, int which, int64_t hp,
+                               Tc* coef) {
+  const int R = t.R, n0 = t.n0, nn = n0 * n0;
+  const int total = subtree_nodes(R, G) * R * nn;
+  const Tc* base = which == 0 ? t.U : (which == 1 ? t.V : t.W);
+  const int cr = which == 1 ? 1 : 0;  // row stream: pi1/s1 (u^, w^) or pi2/s2 (v^)
+  const int cc = which == 0 ? 1 : 2;  // column stream: pi2/s2 (u^) or pi3/s3 (v^, w^)
+  const Tc sc = which == 2 ? t.scale : (Tc)1;
+  const int nthreads = blockDim.x * blockDim.y;
+  for (int e = threadIdx.y * blockDim.x + threadIdx.x; e < total; e += nthreads) {
+    const int local = e / (R * nn);
+    const int rem = e - local * R * nn;
+    const int r = rem / nn, ab = rem - r * nn, ra = ab / n0, cb = ab - ra * n0;
+    int j = 0, start = 0, width = 1;
+    while (local >= start + width) {
+      start += width;
+      width *= R;
+      ++j;
+    }
+    int64_t rj = 1;
+    for (int i = 0; i < j; ++i) rj *= R;
+    const int64_t heap = hp * rj + (int64_t)local;  // descendant of hp: hp*R^j + sum_{i<j} R^i + q
+    const uint64_t w = t.per_level ? t.draw[a.depth + j] : t.draw[a.dbase[j] + (heap - a.dfirst[j])];
+    const Tc v = base[(draw_perm(w, cr, ra) * n0 + draw_perm(w, cc, cb)) * R + r];
+    coef[e] = sc * v * (Tc)draw_sign(w, cr, ra) * (Tc)draw_sign(w, cc, cb);
+  }
+}
 
 // ------------------------------------------------------------------ encode walk
-template <typename Tc, int N0, int G>
+template <typename Tc, int N0, int G, int VEC>
 struct EncodeWalk {
   static constexpr int W = cpow(N0, G), WC = W / N0;
   template <class Emit>
-  __device__ __forceinline__ static void go(const Tables<Tc>& t, const PassArgs& a, const Tc* base, int cr,
-                                            int cc, int rel, int64_t node, int64_t path, const Tc (&in)[W * W],
-                                            Emit& emit) {
-    const uint64_t w = node_draw(t, a, rel, node);
-    int prow[N0], pcol[N0];
-    Tc srow[N0], scol[N0];
-#pragma unroll
-    for (int j = 0; j < N0; ++j) {
-      prow[j] = draw_perm(w, cr, j);
-      pcol[j] = draw_perm(w, cc, j);
-      srow[j] = (Tc)draw_sign(w, cr, j);
-      scol[j] = (Tc)draw_sign(w, cc, j);
-    }
-    const int R = t.R;
+  __device__ __forceinline__ static void go(const Tc* coef, int R, int j, int q, int64_t path,
+                                            const Tc (&in)[W * W][VEC], Emit& emit) {
+    const Tc* row = coef + (size_t)local_id(R, j, q) * R * (N0 * N0);
     for (int r = 0; r < R; ++r) {
-      Tc cin[WC * WC];
+      const Tc* c = row + r * (N0 * N0);
+      Tc cin[WC * WC][VEC];
 #pragma unroll
-      for (int e = 0; e < WC * WC; ++e) cin[e] = (Tc)0;
+      for (int e = 0; e < WC * WC; ++e)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) cin[e][v] = (Tc)0;
 #pragma unroll
       for (int k = 0; k < N0; ++k)
 #pragma unroll
         for (int l = 0; l < N0; ++l) {
-          const Tc coef = base[(prow[k] * N0 + pcol[l]) * R + r] * srow[k] * scol[l];
-          if (coef != (Tc)0) {
+          const Tc cf = c[k * N0 + l];
+          if (cf != (Tc)0) {
 #pragma unroll
             for (int u = 0; u < WC; ++u)
 #pragma unroll
-              for (int v = 0; v < WC; ++v)
-                cin[u * WC + v] = cin[u * WC + v] + coef * in[(k * WC + u) * W + (l * WC + v)];
+              for (int w = 0; w < WC; ++w)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                  cin[u * WC + w][v] = cin[u * WC + w][v] + cf * in[(k * WC + u) * W + (l * WC + w)][v];
           }
         }
-      EncodeWalk<Tc, N0, G - 1>::go(t, a, base, cr, cc, rel + 1, heap_child(node, r, R), path * R + r, cin, emit);
+      EncodeWalk<Tc, N0, G - 1, VEC>::go(coef, R, j + 1, q * R + r, path * R + r, cin, emit);
     }
   }
 };
 
-template <typename Tc, int N0>
-struct EncodeWalk<Tc, N0, 0> {
+template <typename Tc, int N0, int VEC>
+struct EncodeWalk<Tc, N0, 0, VEC> {
   template <class Emit>
-  __device__ __forceinline__ static void go(const Tables<Tc>&, const PassArgs&, const Tc*, int, int, int,
-                                            int64_t, int64_t path, const Tc (&in)[1], Emit& emit) {
+  __device__ __forceinline__ static void go(const Tc*, int, int, int, int64_t path, const Tc (&in)[1][VEC],
+                                            Emit& emit) {
     emit(path, in[0]);
   }
 };
 
-template <typename Tc, int S>
+// Store VEC adjacent outputs (and their lo panel when split).
+template <typename Tc, int S, int VEC>
 struct EncodeEmit {
   using Tout = typename StoreType<S>::T;
-  Tout* Y;       // this parent's first output operand
+  Tout* Y;
   int64_t strideY, off, kpanel;
   int split;
-  __device__ __forceinline__ void operator()(int64_t path, Tc v) {
+  __device__ __forceinline__ void operator()(int64_t path, const Tc (&val)[VEC]) {
     Tout* dst = Y + path * strideY + off;
-    const Tout hi = to_store<S>((double)v);
-    dst[0] = hi;
-    if (split) dst[kpanel] = to_store<S>((double)(v - (Tc)from_store<S>(hi)));
+    Tout hi[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) hi[v] = to_store<S>((double)val[v]);
+    store_vec<Tout, VEC>(dst, hi);
+    if (split) {
+      Tout lo[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(val[v] - (Tc)from_store<S>(hi[v])));
+      store_vec<Tout, VEC>(dst + kpanel, lo);
+    }
   }
 };
 
-template <typename Tin, typename Tc, int N0, int G, int S>
+// Grid: x over row segments of kThreadsX * VEC positions, y over rows, z over parents.
+template <typename Tin, typename Tc, int N0, int G, int S, int VEC>
 __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_constant__ Tables<Tc> t,
                                                                 const PassArgs a) {
   constexpr int W = cpow(N0, G);
   using Tout = typename StoreType<S>::T;
-  const int64_t x = (int64_t)blockIdx.x * kThreadsX + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
+  const int64_t x = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
   const int64_t y = blockIdx.y;
-  if (x >= a.cols_out) return;
-  const bool valid = y < a.nb && x < a.nb;
-  const int cr = a.tensor == 0 ? 0 : 1;  // u^: (pi1, s1) rows, (pi2, s2) cols
-  const int cc = a.tensor == 0 ? 1 : 2;  // v^: (pi2, s2) rows, (pi3, s3) cols
-  const Tc* base = a.tensor == 0 ? t.U : t.V;
+  const bool inside = x < a.cols_out;
+  const bool valid = y < a.nb && x < a.nb;  // nb is a multiple of VEC
   const int64_t outs = a.outs_per_parent;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
-    EncodeEmit<Tc, S> emit;
+    __syncthreads();  // the previous parent's readers are done with the tables
+    expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
+    __syncthreads();
+    if (!inside) continue;
+    EncodeEmit<Tc, S, VEC> emit;
     emit.Y = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
     emit.strideY = a.strideY;
     emit.off = y * a.ldy + x;
     emit.kpanel = a.kpanel;
     emit.split = a.split;
     if (!valid) {  // zero padding of the leaf operands
-      for (int64_t q = 0; q < outs; ++q) emit(q, (Tc)0);
+      Tc z[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) z[v] = (Tc)0;
+      for (int64_t q = 0; q < outs; ++q) emit(q, z);
       continue;
     }
     const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
-    Tc in[W * W];
+    Tc in[W * W][VEC];
 #pragma unroll
     for (int k = 0; k < W; ++k)
 #pragma unroll
-      for (int l = 0; l < W; ++l) in[k * W + l] = (Tc)X[(k * a.nb + y) * a.ldx + l * a.nb + x];
-    EncodeWalk<Tc, N0, G>::go(t, a, base, cr, cc, 0, a.node_first + p, 0, in, emit);
+      for (int l = 0; l < W; ++l) {
+        Tin raw[VEC];
+        load_vec<Tin, VEC>(raw, X + (k * a.nb + y) * a.ldx + l * a.nb + x);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) in[k * W + l][v] = (Tc)raw[v];
+      }
+    EncodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, in, emit);
+  }
+}
+
+// Final encode pass writing each output transposed (T^T, rows n, K contiguous), for tensor-core
+// kinds that take both operands K-major.  The CTA owns 32 (x) x 8 (y) positions; every
+// output goes through a double-buffered shared tile so that each warp stores runs of 8
+// consecutive elements of a transposed row.  All threads walk the subtree (padding positions
+// on zeros) so that every thread reaches the same barriers.
+template <typename Tc, int S>
+struct TransposedEmit {
+  using Tout = typename StoreType<S>::T;
+  Tc (*tile)[32][9];
+  Tout* Y;
+  int64_t strideY, ldy, kpanel, x0, y0;
+  int split, tx, ty, tid, buf;
+  __device__ __forceinline__ void operator()(int64_t path, const Tc (&val)[1]) {
+    tile[buf][tx][ty] = val[0];
+    __syncthreads();
+    const int r = tid >> 3, c = tid & 7;
+    const Tc w = tile[buf][r][c];
+    Tout* dst = Y + path * strideY + (x0 + r) * ldy + (y0 + c);
+    const Tout hi = to_store<S>((double)w);
+    dst[0] = hi;
+    if (split) dst[kpanel] = to_store<S>((double)(w - (Tc)from_store<S>(hi)));
+    buf ^= 1;
+  }
+};
+
+template <typename Tin, typename Tc, int N0, int G, int S>
+__global__ void __launch_bounds__(256) encode_pass_trans_kernel(const __grid_constant__ Tables<Tc> t,
+                                                               const PassArgs a) {
+  constexpr int W = cpow(N0, G);
+  using Tout = typename StoreType<S>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
+  __shared__ Tc tile[2][32][9];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t x0 = (int64_t)blockIdx.x * 32, y0 = (int64_t)blockIdx.y * 8;
+  const int64_t x = x0 + tx, y = y0 + ty;
+  const bool valid = y < a.nb && x < a.nb;
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    __syncthreads();
+    expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
+    __syncthreads();
+    TransposedEmit<Tc, S> emit;
+    emit.tile = tile;
+    emit.Y = static_cast<Tout*>(a.Y) + p * a.outs_per_parent * a.strideY;
+    emit.strideY = a.strideY;
+    emit.ldy = a.ldy;
+    emit.kpanel = a.kpanel;
+    emit.x0 = x0;
+    emit.y0 = y0;
+    emit.split = a.split;
+    emit.tx = tx;
+    emit.ty = ty;
+    emit.tid = ty * 32 + tx;
+    emit.buf = 0;
+    const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
+    Tc in[W * W][1];
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+#pragma unroll
+      for (int l = 0; l < W; ++l)
+        in[k * W + l][0] = valid ? (Tc)X[(k * a.nb + y) * a.ldx + l * a.nb + x] : (Tc)0;
+    EncodeWalk<Tc, N0, G, 1>::go(coef, t.R, 0, 0, 0, in, emit);
   }
 }
 
 // ------------------------------------------------------------------ decode walk
-template <typename Tc, int N0, int G>
+template <typename Tc, int N0, int G, int VEC>
 struct DecodeWalk {
   static constexpr int W = cpow(N0, G), WC = W / N0;
   template <class Fetch>
-  __device__ __forceinline__ static void go(const Tables<Tc>& t, const PassArgs& a, int rel, int64_t node,
-                                            int64_t path, Tc (&out)[W * W], Fetch& fetch) {
-    const uint64_t w = node_draw(t, a, rel, node);
-    int p1[N0], p3[N0];
-    Tc s1[N0], s3[N0];
+  __device__ __forceinline__ static void go(const Tc* coef, int R, int j, int q, int64_t path,
+                                            Tc (&out)[W * W][VEC], Fetch& fetch) {
+    const Tc* row = coef + (size_t)local_id(R, j, q) * R * (N0 * N0);
 #pragma unroll
-    for (int j = 0; j < N0; ++j) {
-      p1[j] = draw_perm(w, 0, j);
-      p3[j] = draw_perm(w, 2, j);
-      s1[j] = (Tc)draw_sign(w, 0, j);
-      s3[j] = (Tc)draw_sign(w, 2, j);
-    }
+    for (int e = 0; e < W * W; ++e)
 #pragma unroll
-    for (int e = 0; e < W * W; ++e) out[e] = (Tc)0;
-    const int R = t.R;
+      for (int v = 0; v < VEC; ++v) out[e][v] = (Tc)0;
     for (int r = 0; r < R; ++r) {
-      Tc cout[WC * WC];
-      DecodeWalk<Tc, N0, G - 1>::go(t, a, rel + 1, heap_child(node, r, R), path * R + r, cout, fetch);
+      Tc cout[WC * WC][VEC];
+      DecodeWalk<Tc, N0, G - 1, VEC>::go(coef, R, j + 1, q * R + r, path * R + r, cout, fetch);
+      const Tc* c = row + r * (N0 * N0);
 #pragma unroll
       for (int i = 0; i < N0; ++i)
 #pragma unroll
-        for (int j = 0; j < N0; ++j) {
-          const Tc wv = t.scale * t.W[(p1[i] * N0 + p3[j]) * R + r] * s1[i] * s3[j];
+        for (int jj = 0; jj < N0; ++jj) {
+          const Tc wv = c[i * N0 + jj];
           if (wv != (Tc)0) {
 #pragma unroll
             for (int u = 0; u < WC; ++u)
 #pragma unroll
-              for (int v = 0; v < WC; ++v)
-                out[(i * WC + u) * W + (j * WC + v)] = out[(i * WC + u) * W + (j * WC + v)] + wv * cout[u * WC + v];
+              for (int w = 0; w < WC; ++w)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                  out[(i * WC + u) * W + (jj * WC + w)][v] =
+                      out[(i * WC + u) * W + (jj * WC + w)][v] + wv * cout[u * WC + w][v];
           }
         }
     }
   }
 };
 
-template <typename Tc, int N0>
-struct DecodeWalk<Tc, N0, 0> {
+// Bottom node: its R children are leaves of the walk; they are loaded eight at a time.
+template <typename Tc, int N0, int VEC>
+struct DecodeWalk<Tc, N0, 1, VEC> {
+  static constexpr int W = N0;
   template <class Fetch>
-  __device__ __forceinline__ static void go(const Tables<Tc>&, const PassArgs&, int, int64_t, int64_t path,
-                                            Tc (&out)[1], Fetch& fetch) {
-    out[0] = fetch(path);
+  __device__ __forceinline__ static void go(const Tc* coef, int R, int j, int q, int64_t path,
+                                            Tc (&out)[W * W][VEC], Fetch& fetch) {
+    const Tc* row = coef + (size_t)local_id(R, j, q) * R * (N0 * N0);
+#pragma unroll
+    for (int e = 0; e < W * W; ++e)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) out[e][v] = (Tc)0;
+    constexpr int B = 8;
+    for (int r0 = 0; r0 < R; r0 += B) {
+      Tc m[B][VEC];
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        if (r0 + b < R) fetch(path * R + r0 + b, m[b]);
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (r0 + b < R) {
+          const Tc* c = row + (r0 + b) * (N0 * N0);
+#pragma unroll
+          for (int e = 0; e < N0 * N0; ++e) {
+            const Tc wv = c[e];
+            if (wv != (Tc)0) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) out[e][v] = out[e][v] + wv * m[b][v];
+            }
+          }
+        }
+      }
+    }
   }
 };
 
-template <typename Tm, typename To, typename Tc, int N0, int G>
+template <typename Tm, typename Tc, int VEC>
+struct DecodeFetch {
+  const Tm* M;
+  int64_t strideM, off;
+  __device__ __forceinline__ void operator()(int64_t path, Tc (&dst)[VEC]) const {
+    Tm raw[VEC];
+    load_vec<Tm, VEC>(raw, M + path * strideM + off);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) dst[v] = (Tc)raw[v];
+  }
+};
+
+template <typename Tm, typename To, typename Tc, int N0, int G, int VEC>
 __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_constant__ Tables<Tc> t,
                                                                 const PassArgs a) {
   constexpr int W = cpow(N0, G);
-  const int64_t x = (int64_t)blockIdx.x * kThreadsX + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
+  const int64_t x = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
   const int64_t y = blockIdx.y;
-  if (x >= a.nb || y >= a.nb) return;
+  const bool valid = x < a.nb && y < a.nb;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
-    const Tm* M = static_cast<const Tm*>(a.X) + p * a.outs_per_parent * a.strideX;
-    const int64_t off = y * a.ldx + x;
-    const int64_t sM = a.strideX;
-    auto fetch = [M, off, sM](int64_t path) -> Tc { return (Tc)M[path * sM + off]; };
-    Tc out[W * W];
-    DecodeWalk<Tc, N0, G>::go(t, a, 0, a.node_first + p, 0, out, fetch);
+    __syncthreads();
+    expand_subtree(t, a, G, 2, a.node_first + p, coef);
+    __syncthreads();
+    if (!valid) continue;
+    DecodeFetch<Tm, Tc, VEC> fetch;
+    fetch.M = static_cast<const Tm*>(a.X) + p * a.outs_per_parent * a.strideX;
+    fetch.strideM = a.strideX;
+    fetch.off = y * a.ldx + x;
+    Tc out[W * W][VEC];
+    DecodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, out, fetch);
     To* P = static_cast<To*>(a.Y) + p * a.strideY;
 #pragma unroll
     for (int k = 0; k < W; ++k)
 #pragma unroll
-      for (int l = 0; l < W; ++l) P[(k * a.nb + y) * a.ldy + l * a.nb + x] = (To)out[k * W + l];
+      for (int l = 0; l < W; ++l) {
+        To o[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = (To)out[k * W + l][v];
+        store_vec<To, VEC>(P + (k * a.nb + y) * a.ldy + l * a.nb + x, o);
+      }
   }
 }
 
-inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents) {
+inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
-  return dim3((unsigned)((cols + kThreadsX - 1) / kThreadsX), (unsigned)rows, (unsigned)gz);
+  const int64_t span = (int64_t)kThreadsX * vec;
+  return dim3((unsigned)((cols + span - 1) / span), (unsigned)rows, (unsigned)gz);
+}
+
+template <typename K>
+cudaError_t prep(K kern, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+inline bool aligned(const void* p, size_t bytes) { return ((uintptr_t)p % bytes) == 0; }
+
+template <typename Tin, typename Tc, int S, int N0, int G>
+cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a, cudaStream_t st) {
+  using Tout = typename StoreType<S>::T;
+  const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
+  if (a.trans) {
+    if (a.rows_out % 8 || a.cols_out % 32 || a.rows_out != a.cols_out) return cudaErrorInvalidValue;
+    const int64_t gz = a.parents < 65535 ? a.parents : 65535;
+    const dim3 grid((unsigned)(a.cols_out / 32), (unsigned)(a.rows_out / 8), (unsigned)gz), block(32, 8);
+    auto kern = encode_pass_trans_kernel<Tin, Tc, N0, G, S>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, smem, st>>>(t, a);
+    return cudaGetLastError();
+  }
+  constexpr int VEC = Vec<Tc, N0, G>::value;
+  const bool vec_ok = a.nb % VEC == 0 && a.cols_out % VEC == 0 && a.ldx % VEC == 0 && a.ldy % VEC == 0 &&
+                      a.kpanel % VEC == 0 && a.strideX % VEC == 0 && a.strideY % VEC == 0 &&
+                      aligned(a.X, VEC * sizeof(Tin)) && aligned(a.Y, VEC * sizeof(Tout));
+  if (vec_ok) {
+    auto kern = encode_pass_kernel<Tin, Tc, N0, G, S, VEC>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<pass_grid(a.rows_out, a.cols_out, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
+  } else {
+    auto kern = encode_pass_kernel<Tin, Tc, N0, G, S, 1>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<pass_grid(a.rows_out, a.cols_out, a.parents, 1), kThreadsX, smem, st>>>(t, a);
+  }
+  return cudaGetLastError();
 }
 
 template <typename Tin, typename Tc, int S, int N0>
 cudaError_t enc_g(const Tables<Tc>& t, const PassArgs& a, int g, cudaStream_t st) {
-  const dim3 grid = pass_grid(a.rows_out, a.cols_out, a.parents);
   switch (g) {
-    case 1: encode_pass_kernel<Tin, Tc, N0, 1, S><<<grid, kThreadsX, 0, st>>>(t, a); break;
+    case 1: return enc_one<Tin, Tc, S, N0, 1>(t, a, st);
     case 2:
-      if constexpr (N0 <= 3) {
-        encode_pass_kernel<Tin, Tc, N0, 2, S><<<grid, kThreadsX, 0, st>>>(t, a);
-        break;
-      }
-      return cudaErrorInvalidValue;
+      if constexpr (N0 <= 3) return enc_one<Tin, Tc, S, N0, 2>(t, a, st);
+      break;
     case 3:
-      if constexpr (N0 == 2) {
-        encode_pass_kernel<Tin, Tc, N0, 3, S><<<grid, kThreadsX, 0, st>>>(t, a);
-        break;
-      }
-      return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
+      if constexpr (N0 == 2) return enc_one<Tin, Tc, S, N0, 3>(t, a, st);
+      break;
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 template <typename Tin, typename Tc, int S>
@@ -242,26 +483,38 @@ cudaError_t enc_n0(const Tables<Tc>& t, const PassArgs& a, int n0, int g, cudaSt
   return cudaErrorInvalidValue;
 }
 
-template <typename Tm, typename To, typename Tc, int N0>
-cudaError_t dec_g(const Tables<Tc>& t, const PassArgs& a, int g, cudaStream_t st) {
-  const dim3 grid = pass_grid(a.nb, a.nb, a.parents);
-  switch (g) {
-    case 1: decode_pass_kernel<Tm, To, Tc, N0, 1><<<grid, kThreadsX, 0, st>>>(t, a); break;
-    case 2:
-      if constexpr (N0 <= 3) {
-        decode_pass_kernel<Tm, To, Tc, N0, 2><<<grid, kThreadsX, 0, st>>>(t, a);
-        break;
-      }
-      return cudaErrorInvalidValue;
-    case 3:
-      if constexpr (N0 == 2) {
-        decode_pass_kernel<Tm, To, Tc, N0, 3><<<grid, kThreadsX, 0, st>>>(t, a);
-        break;
-      }
-      return cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
+template <typename Tm, typename To, typename Tc, int N0, int G>
+cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a, cudaStream_t st) {
+  constexpr int VEC = Vec<Tc, N0, G>::value;
+  const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
+  const bool vec_ok = a.nb % VEC == 0 && a.ldx % VEC == 0 && a.ldy % VEC == 0 && a.strideX % VEC == 0 &&
+                      a.strideY % VEC == 0 && aligned(a.X, VEC * sizeof(Tm)) && aligned(a.Y, VEC * sizeof(To));
+  if (vec_ok) {
+    auto kern = decode_pass_kernel<Tm, To, Tc, N0, G, VEC>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<pass_grid(a.nb, a.nb, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
+  } else {
+    auto kern = decode_pass_kernel<Tm, To, Tc, N0, G, 1>;
+    cudaError_t e = prep(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<pass_grid(a.nb, a.nb, a.parents, 1), kThreadsX, smem, st>>>(t, a);
   }
   return cudaGetLastError();
+}
+
+template <typename Tm, typename To, typename Tc, int N0>
+cudaError_t dec_g(const Tables<Tc>& t, const PassArgs& a, int g, cudaStream_t st) {
+  switch (g) {
+    case 1: return dec_one<Tm, To, Tc, N0, 1>(t, a, st);
+    case 2:
+      if constexpr (N0 <= 3) return dec_one<Tm, To, Tc, N0, 2>(t, a, st);
+      break;
+    case 3:
+      if constexpr (N0 == 2) return dec_one<Tm, To, Tc, N0, 3>(t, a, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename Tm, typename To, typename Tc>
@@ -274,7 +527,8 @@ cudaError_t dec_n0(const Tables<Tc>& t, const PassArgs& a, int n0, int g, cudaSt
   return cudaErrorInvalidValue;
 }
 
-// Identity "encode" of the single leaf when L = 0: conversion, padding and split panels.
+// Identity "encode" of the single leaf when L = 0: conversion, padding and split panels
+// (output position (y, x), or (x, y) when a.trans: then the block is read down columns).
 template <typename Tin, int S>
 __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) {
   using Tout = typename StoreType<S>::T;
@@ -282,7 +536,8 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
   const int64_t y = blockIdx.y;
   if (x >= a.cols_out) return;
   const Tin* X = static_cast<const Tin*>(a.X);
-  const double v = (y < a.nb && x < a.nb) ? (double)X[y * a.ldx + x] : 0.0;
+  const int64_t sy = a.trans ? x : y, sx = a.trans ? y : x;  // source entry
+  const double v = (sy < a.nb && sx < a.nb) ? (double)X[sy * a.ldx + sx] : 0.0;
   Tout* dst = static_cast<Tout*>(a.Y) + y * a.ldy + x;
   const Tout hi = to_store<S>(v);
   dst[0] = hi;
@@ -293,11 +548,13 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 
 int max_levels_per_pass(int n0) { return n0 == 2 ? 3 : (n0 == 3 ? 2 : 1); }
 
+size_t pass_smem_bytes(int R, int n0, int g, int es) { return (size_t)subtree_nodes(R, g) * R * n0 * n0 * es; }
+
 cudaError_t launch_encode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, int io, int store,
                                cudaStream_t st) {
   if (io != RBC_IO_F64 || store != kStoreF64) return cudaErrorInvalidValue;
   if (g == 0) {
-    copy_leaf_kernel<double, kStoreF64><<<pass_grid(a.rows_out, a.cols_out, 1), kThreadsX, 0, st>>>(a);
+    copy_leaf_kernel<double, kStoreF64><<<pass_grid(a.rows_out, a.cols_out, 1, 1), kThreadsX, 0, st>>>(a);
     return cudaGetLastError();
   }
   return enc_n0<double, double, kStoreF64>(t, a, n0, g, st);
@@ -307,7 +564,7 @@ cudaError_t launch_encode_pass(const Tables<float>& t, const PassArgs& a, int n0
                                cudaStream_t st) {
   if (io != RBC_IO_F32) return cudaErrorInvalidValue;
   if (g == 0) {
-    const dim3 grid = pass_grid(a.rows_out, a.cols_out, 1);
+    const dim3 grid = pass_grid(a.rows_out, a.cols_out, 1, 1);
     switch (store) {
       case kStoreF32: copy_leaf_kernel<float, kStoreF32><<<grid, kThreadsX, 0, st>>>(a); break;
       case kStoreTF32: copy_leaf_kernel<float, kStoreTF32><<<grid, kThreadsX, 0, st>>>(a); break;

@@ -29,6 +29,7 @@ struct PassArgs {
   int depth;
   int tensor;     // encode: 0 left operand (u^), 1 right operand (v^)
   int split;      // encode: write [hi | lo] panels
+  int trans;      // encode, last pass: write each output transposed
   int64_t kpanel;
   int64_t dbase[kMaxLevels];
   int64_t dfirst[kMaxLevels];

@@ -204,6 +204,7 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
     a.outs_per_parent = 1;
     a.split = lo.split;
     a.kpanel = lo.mp;
+    a.trans = tensor == 1 && lo.store == kStoreTF32;
     cudaError_t e = launch_encode_pass(tab, a, n0, 0, io, lo.store, st);
     ++g_launches;
     return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
@@ -236,6 +237,8 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
         a.cols_out = lo.mp;
         a.split = lo.split;
         a.kpanel = lo.mp;
+        // tf32 tensor-core leaves take T K-major: write T^T
+        a.trans = tensor == 1 && lo.store == kStoreTF32;
       } else {
         a.Y = ws + enc[d + g] + (size_t)c0 * outs * nb * nb * lo.es_io;
         a.ldy = nb;

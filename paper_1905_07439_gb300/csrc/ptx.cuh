@@ -157,13 +157,14 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 }
 
 // Descriptor of an MN-major tile with the 128-byte swizzle: atoms of 128 bytes along MN x 8
-// rows along K (1024 bytes); `lbo` = byte stride between atoms along MN, stride-dimension
-// byte offset 1024 = between 8-row groups along K.
-__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t lbo) {
+// rows along K (1024 bytes).  `mn_stride` = byte stride between atoms along MN (stride-
+// dimension field), `k_stride` = byte stride between 8-row groups along K (leading-dimension
+// field).
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t mn_stride, uint32_t k_stride) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((k_stride >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((mn_stride >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
   return d;

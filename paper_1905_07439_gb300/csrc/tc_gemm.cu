@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int KINSTR = KIND == 0 ? 16 : 8;   // K elements per MMA instruction
   constexpr uint32_t B_ATOM = KELEM * 128;     // one MN atom column of B: KELEM rows x 128 B
   constexpr int B_BOXES = BN / (kRowBytes / (KIND == 0 ? 2 : 4));
+  // kind::f16 reads T MN-major (as stored); kind::tf32 takes only K-major operands, so its
+  // right operand is stored transposed (T^T, rows n) and loaded like S.
+  constexpr bool BMN = KIND == 0;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -139,14 +142,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int32_t kx = kb * KELEM;
           ptx::tma_load_2d(st, &tmA, &aux->full[s], kx, rowA);
           if (SPLIT) ptx::tma_load_2d(st + A_BYTES, &tmA, &aux->full[s], kx + p.kpanel, rowA);
-          const int32_t rowB = (int32_t)(leaf * p.mp) + kx;
-          constexpr int NBOX = kRowBytes / (KIND == 0 ? 2 : 4);
+          if constexpr (BMN) {
+            const int32_t rowB = (int32_t)(leaf * p.mp) + kx;
+            constexpr int NBOX = kRowBytes / (KIND == 0 ? 2 : 4);
 #pragma unroll
-          for (int j = 0; j < B_BOXES; ++j) {
-            ptx::tma_load_2d(st + P * A_BYTES + j * B_ATOM, &tmB, &aux->full[s], colB + j * NBOX, rowB);
-            if (SPLIT)
-              ptx::tma_load_2d(st + P * A_BYTES + B_BYTES + j * B_ATOM, &tmB, &aux->full[s],
-                               colB + j * NBOX + p.kpanel, rowB);
+            for (int j = 0; j < B_BOXES; ++j) {
+              ptx::tma_load_2d(st + P * A_BYTES + j * B_ATOM, &tmB, &aux->full[s], colB + j * NBOX, rowB);
+              if (SPLIT)
+                ptx::tma_load_2d(st + P * A_BYTES + B_BYTES + j * B_ATOM, &tmB, &aux->full[s],
+                                 colB + j * NBOX + p.kpanel, rowB);
+            }
+          } else {
+            const int32_t rowB = (int32_t)(leaf * p.mp) + colB;
+            ptx::tma_load_2d(st + P * A_BYTES, &tmB, &aux->full[s], kx, rowB);
+            if (SPLIT) ptx::tma_load_2d(st + P * A_BYTES + B_BYTES, &tmB, &aux->full[s], kx + p.kpanel, rowB);
           }
           armed |= 1u << s;
           last_par = (last_par & ~(1u << s)) | (ph << s);
@@ -188,11 +197,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < KSTEPS; ++k) {
             const uint64_t ahi = ptx::desc_sw128(a0 + k * 32);
-            const uint64_t bhi = ptx::desc_sw128_mn(b0 + k * KINSTR * 128, B_ATOM);
+            const uint64_t bhi = BMN ? ptx::desc_sw128_mn(b0 + k * KINSTR * 128, 1024, B_ATOM)
+                                     : ptx::desc_sw128(b0 + k * 32);
             const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
             if (SPLIT) {
               const uint64_t alo = ptx::desc_sw128(a0 + A_BYTES + k * 32);
-              const uint64_t blo = ptx::desc_sw128_mn(b0 + B_BYTES + k * KINSTR * 128, B_ATOM);
+              const uint64_t blo = BMN ? ptx::desc_sw128_mn(b0 + B_BYTES + k * KINSTR * 128, 1024, B_ATOM)
+                                       : ptx::desc_sw128(b0 + B_BYTES + k * 32);
               ptx::mma<KIND>(d_tmem, ahi, blo, p.idesc, acc);
               ptx::mma<KIND>(d_tmem, alo, bhi, p.idesc, 1u);
               ptx::mma<KIND>(d_tmem, ahi, bhi, p.idesc, 1u);
@@ -363,7 +374,8 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   CUtensorMap ma, mb;
   // A: rows of S (K contiguous), boxes 128 rows x 128 B.  B: rows of T are k, n contiguous;
   // boxes of (K elements per stage) rows x 128 B of n.
-  if (!make_map(&ma, a.S, dt, es, a.K, rows, BM) || !make_map(&mb, a.T, dt, es, a.K, rows, kRowBytes / es))
+  if (!make_map(&ma, a.S, dt, es, a.K, rows, BM) ||
+      !make_map(&mb, a.T, dt, es, a.K, rows, tf32 ? bn : kRowBytes / es))
     return cudaErrorInvalidValue;
   Params p{};
   p.m = a.m;
@@ -376,7 +388,7 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   p.nk = (int)(a.mp / kelem);
   p.kpanel = (int)a.mp;
   const uint32_t fmt = tf32 ? 2u : (a.leaf == RBC_LEAF_F16 ? 0u : 1u);
-  p.idesc = ptx::idesc(fmt, fmt, BM, bn, 1u);
+  p.idesc = ptx::idesc(fmt, fmt, BM, bn, tf32 ? 0u : 1u);
   p.epi = a.store_m ? 2 : (a.direct ? 1 : 0);
   p.C = static_cast<float*>(a.C);
   p.ldc = a.ldc;
