@@ -220,7 +220,8 @@ def run_ours(args):
     leaf_ms, leaf_flops, enc_ms, enc_bytes = 0.0, 0.0, 0.0, 0.0
     per_case = []
     es_leaf = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2}[args.leaf]
-    split = 3 if args.leaf.startswith("3x") else 1
+    split = 3 if args.leaf.startswith("3x") else 1      # MMA passes per leaf product
+    panels = 2 if args.leaf.startswith("3x") else 1     # stored operand panels (hi, lo)
     for i, (nm, n, L) in enumerate(cases):
         U = formula_by_name(nm, 7)[0]
         R, n0 = U.shape[2], U.shape[0]
@@ -233,7 +234,7 @@ def run_ours(args):
         leaf_ms += g
         leaf_flops += lf
         # algorithmic encode bytes: read A, B once, write the leaf operands once
-        eb = 2 * 4 * n * n + 2 * es_leaf * split * R**L * m * m
+        eb = 2 * 4 * n * n + 2 * es_leaf * panels * R**L * m * m
         enc_ms += e
         enc_bytes += eb
         per_case.append({"formula": nm, "n": n, "L": L, "ms": round(tot, 3),

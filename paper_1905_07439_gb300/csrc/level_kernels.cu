@@ -546,7 +546,9 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 
 }  // namespace
 
-int max_levels_per_pass(int n0) { return n0 == 2 ? 3 : (n0 == 3 ? 2 : 1); }
+// Two levels per pass: three-level passes of n0 = 2 hold 64 values per position and run at
+// low occupancy, which measured slower than an extra pass over an intermediate.
+int max_levels_per_pass(int n0) { return n0 <= 3 ? 2 : 1; }
 
 size_t pass_smem_bytes(int R, int n0, int g, int es) { return (size_t)subtree_nodes(R, g) * R * n0 * n0 * es; }
 
