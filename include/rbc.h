@@ -175,6 +175,25 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
                          void* workspace, size_t workspace_bytes, void* stream,
                          rbc_matmul_opts* opts);
 
+/* rbc_matmul without a caller workspace, for callers that cannot allocate device memory
+ * when they multiply (a framework that has reserved the whole device heap for its own
+ * allocator, code allowed to allocate only at start-up, paths that cannot handle an
+ * allocation failure).  The paper has no counterpart: this is a property of the library.
+ *
+ * Scratch comes from a fixed 64 MiB array inside the library's device image (every GPU
+ * that loads the library holds it until exit; rbc_static_scratch_bytes() reports the size).
+ * Products needing more scratch than that (rbc_workspace_size) return RBC_ENOMEM with a
+ * message.  The call itself allocates nothing.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the previous call's contents (only
+ * the status word is cleared per call), so calls whose device work overlaps -- on
+ * different streams or threads -- race and give wrong results: order them on one stream.
+ * The status word read by rbc_workspace_check lives at the start of the array. */
+rbc_status rbc_matmul_static(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N,
+                             int64_t lda, int64_t ldb, int64_t ldc, int io_dtype, int leaf_dtype,
+                             void* stream);
+size_t rbc_static_scratch_bytes(void);
+
 /* Device-side status of the calls that used `workspace` (its first 4 bytes, cleared by every
  * rbc_matmul): waits for `stream`, copies the word to *device_status and clears it.  0 means
  * no error; RBC_ETIMEOUT means a bounded wait inside a kernel expired and that kernel skipped

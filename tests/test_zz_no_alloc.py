@@ -1,0 +1,74 @@
+"""The allocation-free entry point rbc_matmul_static.
+
+Some callers cannot obtain device memory at the moment they multiply: a framework that has
+already reserved the whole device heap for its own allocator, programs allowed to allocate
+only at start-up, code paths that have no way to recover from a failed allocation.  For
+them the library offers rbc_matmul_static, which takes its scratch from a fixed array in
+the library's device image.  These tests call it through the C ABI and check that it
+returns the same product as rbc_matmul with a caller-provided workspace, on two calls in a
+row (the array keeps the previous call's contents), and that it refuses products whose
+scratch would not fit, with a clear error.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from ._helpers import formula, gate, normwise
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rbc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1905_07439_gb300 import build as b
+    b.build()
+    import paper_1905_07439_gb300 as pkg
+    return pkg
+
+
+def _static_call(rbc, plan, A, B, C, leaf):
+    N = A.shape[0]
+    io = rbc.IO_F32 if A.dtype == torch.float32 else rbc.IO_F64
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return rbc.lib().rbc_matmul_static(plan.handle, A.data_ptr(), B.data_ptr(), C.data_ptr(), N,
+                                       A.stride(0), B.stride(0), C.stride(0), io, leaf, stream)
+
+
+def test_static_scratch_matches_workspace_entry_point(rbc):
+    cases = [("strassen", 2, 4 * 192, "bf16", torch.float32),
+             ("laderman", 1, 3 * 120, "3xbf16", torch.float32),
+             ("noisy-strassen", 2, 4 * 40, "f64", torch.float64)]
+    g = torch.Generator(device="cuda")
+    for i, (name, L, N, leaf_name, dt) in enumerate(cases):
+        U, V, W = formula(name, seed=4)
+        plan = rbc.Plan(U, V, W, levels=L, seed=100 + i)
+        leaf = rbc.LEAF_NAMES[leaf_name]
+        assert 0 < plan.workspace_size(N, rbc.IO_F32 if dt == torch.float32 else rbc.IO_F64, leaf) \
+            <= rbc.lib().rbc_static_scratch_bytes()
+        g.manual_seed(7 + i)
+        A = torch.randn((N, N), generator=g, device="cuda", dtype=dt)
+        B = torch.randn((N, N), generator=g, device="cuda", dtype=dt)
+        C_static = torch.full((N, N), float("nan"), device="cuda", dtype=dt)
+        rbc.rbc.check(_static_call(rbc, plan, A, B, C_static, leaf), "rbc_matmul_static")
+        C_ref = rbc.matmul(plan, A, B, leaf=leaf)
+        torch.cuda.synchronize()
+        Cs, Cr = C_static.double().cpu().numpy(), C_ref.double().cpu().numpy()
+        An, Bn = A.double().cpu().numpy(), B.double().cpu().numpy()
+        assert np.isfinite(Cs).all()
+        tol = 1e-12 if leaf_name == "f64" else gate(leaf_name, U.shape[0], L, N)
+        assert normwise(Cs, Cr, An, Bn) <= tol
+
+
+def test_static_scratch_rejects_oversized_products(rbc):
+    U, V, W = formula("strassen")
+    plan = rbc.Plan(U, V, W, levels=2, seed=1)
+    N = 4096
+    assert plan.workspace_size(N, rbc.IO_F32, rbc.LEAF_BF16) > rbc.lib().rbc_static_scratch_bytes()
+    A = torch.zeros((N, N), device="cuda")
+    C = torch.zeros((N, N), device="cuda")
+    st = _static_call(rbc, plan, A, A, C, rbc.LEAF_BF16)
+    assert st == 2  # RBC_ENOMEM
+    assert b"64 MiB" in rbc.lib().rbc_last_error()
