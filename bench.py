@@ -255,8 +255,13 @@ def run_ours(args):
         peak = pk["bf16_tflops_sustained"] * ratio
         peak_note = f"{pk_kind} bf16 sustained x {ratio} (nominal {args.leaf}/bf16 ratio)"
     achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
-    roof = {"kernel": "leaf products + fused decode", "bound": bound, "achieved": round(achieved, 2),
-            "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4), "traffic": None,
+    roof = {"kernel": "tc_gemm_kernel / simt_gemm_kernel: the leaf products of all cases of the step "
+                      "(achieved = their algorithmic flops / their summed event time)",
+            "bound": bound, "achieved": round(achieved, 2),
+            "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
+            "traffic": None,
+            "traffic_note": "per-launch DRAM bytes differ per case; the ncu capture of one launch is summarized "
+                            "in profiles/tc_gemm_noisy_strassen_n4096_L1_3xbf16.md",
             "peak_source": peak_note,
             "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
                        "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}}
@@ -306,6 +311,29 @@ def run_ours(args):
             errors.append({"formula": nm, "n": n, "L": L, "rel_fro_vs_fp64_ab": float(np.sqrt(nr[0] / nr[1]))})
         torch.cuda.synchronize(dev)
 
+    # Our own classical product (L = 0, same leaf mode) on the same inputs, for comparison.
+    classical = {}
+    if not args.no_errors:
+        one = rbc.Plan(*formula_by_name("strassen"), levels=0)
+        for _, n, _ in cases:
+            if str(n) in classical:
+                continue
+            x = inputs[n]
+            wsz = one.workspace_size(n, rbc.IO_F32, leaf)
+            wsc = torch.empty(wsz, dtype=torch.uint8, device=dev)
+            for _ in range(2):
+                rbc.matmul(one, x["A"], x["B"], x["C"], leaf=leaf, workspace=wsc)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                rbc.matmul(one, x["A"], x["B"], x["C"], leaf=leaf, workspace=wsc)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / 3
+            classical[str(n)] = {"ms": round(ms, 3), "eff_tflops": round(2.0 * n**3 / ms / 1e9, 1)}
+            del wsc
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(budget_s=15.0, gpu_check=(plans, cases, inputs, ws, leaf))
@@ -321,7 +349,8 @@ def run_ours(args):
                    "l2": "inputs and per-case workspaces larger than L2 (129 MB)"},
         "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
         "gpu_launches_per_step": launches_per_step,
-        "e2e": e2e, "cpu_baseline": cpu, "cases": per_case, "errors": errors,
+        "e2e": e2e, "cpu_baseline": cpu, "classical_same_leaf": classical, "cases": per_case,
+        "errors": errors,
     }
     if rank == 0:
         print(json.dumps(line))
