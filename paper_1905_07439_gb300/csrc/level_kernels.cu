@@ -163,29 +163,43 @@ struct EncodeWalk<Tc, N0, 0, VEC> {
   }
 };
 
-// Store VEC adjacent outputs (and their lo panel when split).
+// Store VEC adjacent outputs: one vector store when aligned and complete, else element by
+// element up to the output width.
+template <typename T, int VEC>
+__device__ __forceinline__ void store_some(T* dst, const T (&x)[VEC], bool vec, int64_t avail) {
+  if (vec && avail >= VEC) {
+    store_vec<T, VEC>(dst, x);
+  } else {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+      if (v < avail) dst[v] = x[v];
+  }
+}
+
 template <typename Tc, int S, int VEC>
-struct EncodeEmit {
+struct EncodeEmitV {
   using Tout = typename StoreType<S>::T;
   Tout* Y;
-  int64_t strideY, off, kpanel;
+  int64_t strideY, off, kpanel, avail;
   int split;
+  bool vec;
   __device__ __forceinline__ void operator()(int64_t path, const Tc (&val)[VEC]) {
     Tout* dst = Y + path * strideY + off;
     Tout hi[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) hi[v] = to_store<S>((double)val[v]);
-    store_vec<Tout, VEC>(dst, hi);
+    store_some<Tout, VEC>(dst, hi, vec, avail);
     if (split) {
       Tout lo[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(val[v] - (Tc)from_store<S>(hi[v])));
-      store_vec<Tout, VEC>(dst + kpanel, lo);
+      store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
     }
   }
 };
 
 // Grid: x over row segments of kThreadsX * VEC positions, y over rows, z over parents.
+// Positions at or beyond nb (padding up to cols_out / rows_out) encode zeros.
 template <typename Tin, typename Tc, int N0, int G, int S, int VEC>
 __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_constant__ Tables<Tc> t,
                                                                 const PassArgs a) {
@@ -196,20 +210,21 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
   const int64_t x = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
   const int64_t y = blockIdx.y;
   const bool inside = x < a.cols_out;
-  const bool valid = y < a.nb && x < a.nb;  // nb is a multiple of VEC
   const int64_t outs = a.outs_per_parent;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();  // the previous parent's readers are done with the tables
     expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
     __syncthreads();
     if (!inside) continue;
-    EncodeEmit<Tc, S, VEC> emit;
+    EncodeEmitV<Tc, S, VEC> emit;
     emit.Y = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
     emit.strideY = a.strideY;
     emit.off = y * a.ldy + x;
     emit.kpanel = a.kpanel;
     emit.split = a.split;
-    if (!valid) {  // zero padding of the leaf operands
+    emit.vec = a.vstore != 0;
+    emit.avail = a.cols_out - x;
+    if (y >= a.nb || x >= a.nb) {  // padding only: zero outputs
       Tc z[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; ++v) z[v] = (Tc)0;
@@ -217,13 +232,20 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
       continue;
     }
     const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
+    const bool full = a.vload && x + VEC <= a.nb;
     Tc in[W * W][VEC];
 #pragma unroll
     for (int k = 0; k < W; ++k)
 #pragma unroll
       for (int l = 0; l < W; ++l) {
+        const Tin* src = X + (k * a.nb + y) * a.ldx + l * a.nb + x;
         Tin raw[VEC];
-        load_vec<Tin, VEC>(raw, X + (k * a.nb + y) * a.ldx + l * a.nb + x);
+        if (full) {
+          load_vec<Tin, VEC>(raw, src);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) raw[v] = (x + v < a.nb) ? src[v] : (Tin)0;
+        }
 #pragma unroll
         for (int v = 0; v < VEC; ++v) in[k * W + l][v] = (Tc)raw[v];
       }
@@ -371,10 +393,17 @@ struct DecodeWalk<Tc, N0, 1, VEC> {
 template <typename Tm, typename Tc, int VEC>
 struct DecodeFetch {
   const Tm* M;
-  int64_t strideM, off;
+  int64_t strideM, off, avail;
+  bool vec;
   __device__ __forceinline__ void operator()(int64_t path, Tc (&dst)[VEC]) const {
+    const Tm* src = M + path * strideM + off;
     Tm raw[VEC];
-    load_vec<Tm, VEC>(raw, M + path * strideM + off);
+    if (vec && avail >= VEC) {
+      load_vec<Tm, VEC>(raw, src);
+    } else {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) raw[v] = v < avail ? src[v] : (Tm)0;
+    }
 #pragma unroll
     for (int v = 0; v < VEC; ++v) dst[v] = (Tc)raw[v];
   }
@@ -398,9 +427,12 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
     fetch.M = static_cast<const Tm*>(a.X) + p * a.outs_per_parent * a.strideX;
     fetch.strideM = a.strideX;
     fetch.off = y * a.ldx + x;
+    fetch.avail = a.nb - x;
+    fetch.vec = a.vload != 0;
     Tc out[W * W][VEC];
     DecodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, out, fetch);
     To* P = static_cast<To*>(a.Y) + p * a.strideY;
+    const bool vs = a.vstore != 0;
 #pragma unroll
     for (int k = 0; k < W; ++k)
 #pragma unroll
@@ -408,7 +440,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
         To o[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] = (To)out[k * W + l][v];
-        store_vec<To, VEC>(P + (k * a.nb + y) * a.ldy + l * a.nb + x, o);
+        store_some<To, VEC>(P + (k * a.nb + y) * a.ldy + l * a.nb + x, o, vs, a.nb - x);
       }
   }
 }
@@ -428,34 +460,27 @@ cudaError_t prep(K kern, size_t smem) {
 inline bool aligned(const void* p, size_t bytes) { return ((uintptr_t)p % bytes) == 0; }
 
 template <typename Tin, typename Tc, int S, int N0, int G>
-cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a, cudaStream_t st) {
+cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) {
   using Tout = typename StoreType<S>::T;
   const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
-  if (a.trans) {
-    if (a.rows_out % 8 || a.cols_out % 32 || a.rows_out != a.cols_out) return cudaErrorInvalidValue;
-    const int64_t gz = a.parents < 65535 ? a.parents : 65535;
-    const dim3 grid((unsigned)(a.cols_out / 32), (unsigned)(a.rows_out / 8), (unsigned)gz), block(32, 8);
+  if (a_in.trans) {
+    if (a_in.rows_out % 8 || a_in.cols_out % 32 || a_in.rows_out != a_in.cols_out) return cudaErrorInvalidValue;
+    const int64_t gz = a_in.parents < 65535 ? a_in.parents : 65535;
+    const dim3 grid((unsigned)(a_in.cols_out / 32), (unsigned)(a_in.rows_out / 8), (unsigned)gz), block(32, 8);
     auto kern = encode_pass_trans_kernel<Tin, Tc, N0, G, S>;
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, block, smem, st>>>(t, a);
+    kern<<<grid, block, smem, st>>>(t, a_in);
     return cudaGetLastError();
   }
   constexpr int VEC = Vec<Tc, N0, G>::value;
-  const bool vec_ok = a.nb % VEC == 0 && a.cols_out % VEC == 0 && a.ldx % VEC == 0 && a.ldy % VEC == 0 &&
-                      a.kpanel % VEC == 0 && a.strideX % VEC == 0 && a.strideY % VEC == 0 &&
-                      aligned(a.X, VEC * sizeof(Tin)) && aligned(a.Y, VEC * sizeof(Tout));
-  if (vec_ok) {
-    auto kern = encode_pass_kernel<Tin, Tc, N0, G, S, VEC>;
-    cudaError_t e = prep(kern, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<pass_grid(a.rows_out, a.cols_out, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
-  } else {
-    auto kern = encode_pass_kernel<Tin, Tc, N0, G, S, 1>;
-    cudaError_t e = prep(kern, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<pass_grid(a.rows_out, a.cols_out, a.parents, 1), kThreadsX, smem, st>>>(t, a);
-  }
+  PassArgs a = a_in;
+  a.vload = a.nb % VEC == 0 && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
+  a.vstore = a.ldy % VEC == 0 && a.strideY % VEC == 0 && a.kpanel % VEC == 0 && aligned(a.Y, VEC * sizeof(Tout));
+  auto kern = encode_pass_kernel<Tin, Tc, N0, G, S, VEC>;
+  cudaError_t e = prep(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<pass_grid(a.rows_out, a.cols_out, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
   return cudaGetLastError();
 }
 
@@ -484,22 +509,16 @@ cudaError_t enc_n0(const Tables<Tc>& t, const PassArgs& a, int n0, int g, cudaSt
 }
 
 template <typename Tm, typename To, typename Tc, int N0, int G>
-cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a, cudaStream_t st) {
+cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) {
   constexpr int VEC = Vec<Tc, N0, G>::value;
   const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
-  const bool vec_ok = a.nb % VEC == 0 && a.ldx % VEC == 0 && a.ldy % VEC == 0 && a.strideX % VEC == 0 &&
-                      a.strideY % VEC == 0 && aligned(a.X, VEC * sizeof(Tm)) && aligned(a.Y, VEC * sizeof(To));
-  if (vec_ok) {
-    auto kern = decode_pass_kernel<Tm, To, Tc, N0, G, VEC>;
-    cudaError_t e = prep(kern, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<pass_grid(a.nb, a.nb, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
-  } else {
-    auto kern = decode_pass_kernel<Tm, To, Tc, N0, G, 1>;
-    cudaError_t e = prep(kern, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<pass_grid(a.nb, a.nb, a.parents, 1), kThreadsX, smem, st>>>(t, a);
-  }
+  PassArgs a = a_in;
+  a.vload = a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tm));
+  a.vstore = a.nb % VEC == 0 && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
+  auto kern = decode_pass_kernel<Tm, To, Tc, N0, G, VEC>;
+  cudaError_t e = prep(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<pass_grid(a.nb, a.nb, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
   return cudaGetLastError();
 }
 

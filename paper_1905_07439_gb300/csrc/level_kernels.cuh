@@ -30,6 +30,8 @@ struct PassArgs {
   int tensor;     // encode: 0 left operand (u^), 1 right operand (v^)
   int split;      // encode: write [hi | lo] panels
   int trans;      // encode, last pass: write each output transposed
+  int vload;      // set by the launcher: input rows allow VEC-wide vector loads
+  int vstore;     // set by the launcher: output rows allow VEC-wide vector stores
   int64_t kpanel;
   int64_t dbase[kMaxLevels];
   int64_t dfirst[kMaxLevels];

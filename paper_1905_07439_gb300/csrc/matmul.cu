@@ -20,6 +20,8 @@ thread_local int64_t g_launches = 0;  // kernels launched by the current call
 constexpr size_t kStatusBytes = 256;
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+// Leading dimension of an intermediate operand: rows start 16-byte aligned for vector access.
+inline int64_t pad_ld(int64_t n) { return (n + 3) / 4 * 4; }
 
 bool is_tc_leaf(int leaf) {
   return leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_BF16 || leaf == RBC_LEAF_F16 ||
@@ -125,7 +127,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   for (int i = 1; i < lo->passes.count; ++i) {
     const int d = lo->passes.top[i];
     const int64_t nd = lo->m * ipow(n0, L - d);
-    const size_t bytes = align256((size_t)ipow(R, d) * nd * nd * lo->es_io);
+    const size_t bytes = align256((size_t)ipow(R, d) * nd * pad_ld(nd) * lo->es_io);
     lo->encA[d] = off;
     off += bytes;
     lo->encB[d] = off;
@@ -144,7 +146,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
       const int d = lo->passes.top[i];
       const int64_t nd = lo->m * ipow(n0, L - d);
       lo->dec[d] = off;
-      off += align256((size_t)ipow(R, d) * nd * nd * lo->es_acc);
+      off += align256((size_t)ipow(R, d) * nd * pad_ld(nd) * lo->es_acc);
     }
   }
   lo->total = off;
@@ -225,9 +227,9 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
         a.ldx = ldx;
         a.strideX = 0;
       } else {
-        a.X = ws + enc[d] + (size_t)c0 * n_par * n_par * lo.es_io;
-        a.ldx = n_par;
-        a.strideX = n_par * n_par;
+        a.X = ws + enc[d] + (size_t)c0 * n_par * pad_ld(n_par) * lo.es_io;
+        a.ldx = pad_ld(n_par);
+        a.strideX = n_par * pad_ld(n_par);
       }
       if (last) {
         a.Y = leafbuf + (size_t)c0 * outs * lo.mp * lo.K * lo.es_leaf;
@@ -240,9 +242,9 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
         // tf32 tensor-core leaves take T K-major: write T^T
         a.trans = tensor == 1 && lo.store == kStoreTF32;
       } else {
-        a.Y = ws + enc[d + g] + (size_t)c0 * outs * nb * nb * lo.es_io;
-        a.ldy = nb;
-        a.strideY = nb * nb;
+        a.Y = ws + enc[d + g] + (size_t)c0 * outs * nb * pad_ld(nb) * lo.es_io;
+        a.ldy = pad_ld(nb);
+        a.strideY = nb * pad_ld(nb);
         a.rows_out = nb;
         a.cols_out = nb;
       }
@@ -280,18 +282,18 @@ rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t
         a.ldx = lo.mp;
         a.strideX = lo.mp * lo.mp;
       } else {
-        a.X = ws + lo.dec[d + g] + (size_t)c0 * outs * nb * nb * lo.es_acc;
-        a.ldx = nb;
-        a.strideX = nb * nb;
+        a.X = ws + lo.dec[d + g] + (size_t)c0 * outs * nb * pad_ld(nb) * lo.es_acc;
+        a.ldx = pad_ld(nb);
+        a.strideX = nb * pad_ld(nb);
       }
       if (d == 0) {
         a.Y = C;
         a.ldy = ldc;
         a.strideY = 0;
       } else {
-        a.Y = ws + lo.dec[d] + (size_t)c0 * n_par * n_par * lo.es_acc;
-        a.ldy = n_par;
-        a.strideY = n_par * n_par;
+        a.Y = ws + lo.dec[d] + (size_t)c0 * n_par * pad_ld(n_par) * lo.es_acc;
+        a.ldy = pad_ld(n_par);
+        a.strideY = n_par * pad_ld(n_par);
       }
       a.nb = nb;
       a.parents = cnt;

@@ -66,12 +66,22 @@ __device__ __forceinline__ void raise_abort(volatile int* abort, int* status) {
   if (status) atomicExch(status, (int)RBC_ETIMEOUT);
 }
 
+// Tile order within a leaf: groups of kGroupM tile rows, columns swept inside a group, so
+// that the CTAs running at the same time share A row panels and B column panels in L2
+// (a plain row-major order re-streams every B panel from DRAM once per tile row).
+constexpr int kGroupM = 8;
+
 __device__ __forceinline__ void tile_coords(int64_t tile, const Params& p, int64_t* leaf, int* tm, int* tn) {
   const int64_t per_leaf = (int64_t)p.tiles_m * p.tiles_n;
   *leaf = tile / per_leaf;
   const int r = (int)(tile - *leaf * per_leaf);
-  *tm = r / p.tiles_n;
-  *tn = r - *tm * p.tiles_n;
+  const int per_group = kGroupM * p.tiles_n;
+  const int g = r / per_group;
+  const int first_m = g * kGroupM;
+  const int gm = min(kGroupM, p.tiles_m - first_m);
+  const int w = r - g * per_group;
+  *tm = first_m + w % gm;
+  *tn = w / gm;
 }
 
 template <int KIND, int SPLIT, int BN, int STAGES>
