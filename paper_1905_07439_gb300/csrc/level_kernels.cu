@@ -200,7 +200,9 @@ struct EncodeEmitV {
 
 // Grid: x over row segments of kThreadsX * VEC positions, y over rows, z over parents.
 // Positions at or beyond nb (padding up to cols_out / rows_out) encode zeros.
-template <typename Tin, typename Tc, int N0, int G, int S, int VEC>
+// FAST: every access of the launch is aligned and complete (nb and the output width are
+// multiples of VEC), so loads and stores are plain vectors without per-element checks.
+template <typename Tin, typename Tc, int N0, int G, int S, int VEC, bool FAST>
 __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_constant__ Tables<Tc> t,
                                                                 const PassArgs a) {
   constexpr int W = cpow(N0, G);
@@ -222,8 +224,8 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
     emit.off = y * a.ldy + x;
     emit.kpanel = a.kpanel;
     emit.split = a.split;
-    emit.vec = a.vstore != 0;
-    emit.avail = a.cols_out - x;
+    emit.vec = FAST || a.vstore != 0;
+    emit.avail = FAST ? VEC : a.cols_out - x;
     if (y >= a.nb || x >= a.nb) {  // padding only: zero outputs
       Tc z[VEC];
 #pragma unroll
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
       continue;
     }
     const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
-    const bool full = a.vload && x + VEC <= a.nb;
+    const bool full = FAST || (a.vload && x + VEC <= a.nb);
     Tc in[W * W][VEC];
 #pragma unroll
     for (int k = 0; k < W; ++k)
@@ -409,7 +411,7 @@ struct DecodeFetch {
   }
 };
 
-template <typename Tm, typename To, typename Tc, int N0, int G, int VEC>
+template <typename Tm, typename To, typename Tc, int N0, int G, int VEC, bool FAST>
 __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_constant__ Tables<Tc> t,
                                                                 const PassArgs a) {
   constexpr int W = cpow(N0, G);
@@ -427,12 +429,12 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
     fetch.M = static_cast<const Tm*>(a.X) + p * a.outs_per_parent * a.strideX;
     fetch.strideM = a.strideX;
     fetch.off = y * a.ldx + x;
-    fetch.avail = a.nb - x;
-    fetch.vec = a.vload != 0;
+    fetch.avail = FAST ? VEC : a.nb - x;
+    fetch.vec = FAST || a.vload != 0;
     Tc out[W * W][VEC];
     DecodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, out, fetch);
     To* P = static_cast<To*>(a.Y) + p * a.strideY;
-    const bool vs = a.vstore != 0;
+    const bool vs = FAST || a.vstore != 0;
 #pragma unroll
     for (int k = 0; k < W; ++k)
 #pragma unroll
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
         To o[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] = (To)out[k * W + l][v];
-        store_some<To, VEC>(P + (k * a.nb + y) * a.ldy + l * a.nb + x, o, vs, a.nb - x);
+        store_some<To, VEC>(P + (k * a.nb + y) * a.ldy + l * a.nb + x, o, vs, FAST ? VEC : a.nb - x);
       }
   }
 }
@@ -477,7 +479,8 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   PassArgs a = a_in;
   a.vload = a.nb % VEC == 0 && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
   a.vstore = a.ldy % VEC == 0 && a.strideY % VEC == 0 && a.kpanel % VEC == 0 && aligned(a.Y, VEC * sizeof(Tout));
-  auto kern = encode_pass_kernel<Tin, Tc, N0, G, S, VEC>;
+  const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0;
+  auto kern = fast ? encode_pass_kernel<Tin, Tc, N0, G, S, VEC, true> : encode_pass_kernel<Tin, Tc, N0, G, S, VEC, false>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<pass_grid(a.rows_out, a.cols_out, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
@@ -515,7 +518,8 @@ cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   PassArgs a = a_in;
   a.vload = a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tm));
   a.vstore = a.nb % VEC == 0 && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
-  auto kern = decode_pass_kernel<Tm, To, Tc, N0, G, VEC>;
+  const bool fast = a.vload && a.vstore && a.nb % VEC == 0;
+  auto kern = fast ? decode_pass_kernel<Tm, To, Tc, N0, G, VEC, true> : decode_pass_kernel<Tm, To, Tc, N0, G, VEC, false>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<pass_grid(a.nb, a.nb, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
@@ -565,9 +569,11 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 
 }  // namespace
 
-// Two levels per pass: three-level passes of n0 = 2 hold 64 values per position and run at
-// low occupancy, which measured slower than an extra pass over an intermediate.
-int max_levels_per_pass(int n0) { return n0 <= 3 ? 2 : 1; }
+// Levels per pass: two for n0 = 2 (16 values per position); one for n0 = 3 and 4.  Passes
+// holding 64 or more values per position (three levels of n0 = 2, two of n0 = 3) need about
+// 220 registers, run at low occupancy, and measured slower than an extra pass over an
+// intermediate.
+int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
 
 size_t pass_smem_bytes(int R, int n0, int g, int es) { return (size_t)subtree_nodes(R, g) * R * n0 * n0 * es; }
 

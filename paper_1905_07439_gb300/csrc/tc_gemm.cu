@@ -37,7 +37,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct Params {
   int64_t m, mp, leaves, total_tiles;
-  int nk, tiles_m, tiles_n;
+  int nk, tiles_m, tiles_n, group_m;
   int kpanel;      // element offset of the lo panel along K (split modes)
   uint32_t idesc;
   int epi;         // 0: fused decode by reductions, 1: direct store (L = 0), 2: store M
@@ -66,19 +66,18 @@ __device__ __forceinline__ void raise_abort(volatile int* abort, int* status) {
   if (status) atomicExch(status, (int)RBC_ETIMEOUT);
 }
 
-// Tile order within a leaf: groups of kGroupM tile rows, columns swept inside a group, so
-// that the CTAs running at the same time share A row panels and B column panels in L2
-// (a plain row-major order re-streams every B panel from DRAM once per tile row).
-constexpr int kGroupM = 8;
-
+// Tile order within a leaf: groups of p.group_m tile rows, columns swept inside a group, so
+// that the CTAs running at the same time share A row panels and B column panels in L2 (a
+// plain row-major order re-streams every B panel from DRAM once per tile row when a leaf's
+// operands exceed L2).  group_m = 1 is the row-major order.
 __device__ __forceinline__ void tile_coords(int64_t tile, const Params& p, int64_t* leaf, int* tm, int* tn) {
   const int64_t per_leaf = (int64_t)p.tiles_m * p.tiles_n;
   *leaf = tile / per_leaf;
   const int r = (int)(tile - *leaf * per_leaf);
-  const int per_group = kGroupM * p.tiles_n;
+  const int per_group = p.group_m * p.tiles_n;
   const int g = r / per_group;
-  const int first_m = g * kGroupM;
-  const int gm = min(kGroupM, p.tiles_m - first_m);
+  const int first_m = g * p.group_m;
+  const int gm = min(p.group_m, p.tiles_m - first_m);
   const int w = r - g * per_group;
   *tm = first_m + w % gm;
   *tn = w / gm;
@@ -394,6 +393,9 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   p.tiles_m = (int)(a.mp / BM);
   p.tiles_n = (int)(a.mp / bn);
   p.total_tiles = a.leaves * p.tiles_m * p.tiles_n;
+  // group tile rows only when one leaf's operands do not fit in L2 (about 64 MB per die)
+  const double leaf_bytes = 2.0 * (double)a.mp * (double)a.K * es;
+  p.group_m = leaf_bytes > 64.0 * (1 << 20) ? 8 : 1;
   const int kelem = kRowBytes / es;
   p.nk = (int)(a.mp / kelem);
   p.kpanel = (int)a.mp;
