@@ -39,7 +39,7 @@ __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * c
 template <typename Tc, int N0, int G>
 struct Vec {
   static constexpr int n = cpow(N0, 2 * G);
-  static constexpr int value = sizeof(Tc) == 8 ? (n >= 64 ? 1 : (n >= 16 ? 2 : 4)) : (n >= 64 ? 2 : 4);
+  static constexpr int value = n >= 64 ? 1 : (sizeof(Tc) == 8 && n >= 16 ? 2 : 4);
 };
 
 template <typename T, int VEC>
@@ -252,6 +252,70 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
         for (int v = 0; v < VEC; ++v) in[k * W + l][v] = (Tc)raw[v];
       }
     EncodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, in, emit);
+  }
+}
+
+// Deep encode pass (n0^(2G) >= 64 values per position): the CTA first copies the n0^G x n0^G
+// input row segments of its 128 positions into shared memory with coalesced loads, then each
+// thread forms the first level's children from shared memory and walks the remaining G-1
+// levels in registers.  This keeps the register count near that of a (G-1)-level pass.
+template <typename Tin, typename Tc, int N0, int G, int S>
+__global__ void __launch_bounds__(kThreadsX) encode_pass_staged_kernel(const __grid_constant__ Tables<Tc> t,
+                                                                       const PassArgs a) {
+  constexpr int W = cpow(N0, G), WC = W / N0;
+  using Tout = typename StoreType<S>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
+  const int ncoef = ((subtree_nodes(t.R, G) * t.R * N0 * N0) + 3) & ~3;
+  Tc* in_s = coef + ncoef;  // [W*W][kThreadsX]
+  const int tid = threadIdx.x;
+  const int64_t x0 = (int64_t)blockIdx.x * kThreadsX, x = x0 + tid;
+  const int64_t y = blockIdx.y;
+  const int64_t outs = a.outs_per_parent;
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    __syncthreads();
+    expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
+    const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
+    const bool row_ok = y < a.nb;
+#pragma unroll 4
+    for (int blk = 0; blk < W * W; ++blk) {
+      const int k = blk / W, l = blk - k * W;
+      in_s[blk * kThreadsX + tid] =
+          (row_ok && x < a.nb) ? (Tc)X[(k * a.nb + y) * a.ldx + l * a.nb + x] : (Tc)0;
+    }
+    __syncthreads();
+    if (x >= a.cols_out) continue;
+    EncodeEmitV<Tc, S, 1> emit;
+    emit.Y = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
+    emit.strideY = a.strideY;
+    emit.off = y * a.ldy + x;
+    emit.kpanel = a.kpanel;
+    emit.split = a.split;
+    emit.vec = true;
+    emit.avail = 1;
+    const Tc* row = coef;  // root of the subtree: local id 0
+    const int R = t.R;
+    for (int r = 0; r < R; ++r) {
+      const Tc* c = row + r * (N0 * N0);
+      Tc cin[WC * WC][1];
+#pragma unroll
+      for (int e = 0; e < WC * WC; ++e) cin[e][0] = (Tc)0;
+#pragma unroll
+      for (int k = 0; k < N0; ++k)
+#pragma unroll
+        for (int l = 0; l < N0; ++l) {
+          const Tc cf = c[k * N0 + l];
+          if (cf != (Tc)0) {
+#pragma unroll
+            for (int u = 0; u < WC; ++u)
+#pragma unroll
+              for (int w = 0; w < WC; ++w)
+                cin[u * WC + w][0] =
+                    cin[u * WC + w][0] + cf * in_s[((k * WC + u) * W + (l * WC + w)) * kThreadsX + tid];
+          }
+        }
+      EncodeWalk<Tc, N0, G - 1, 1>::go(coef, R, 1, r, r, cin, emit);
+    }
   }
 }
 
@@ -475,6 +539,15 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
     kern<<<grid, block, smem, st>>>(t, a_in);
     return cudaGetLastError();
   }
+  if constexpr (cpow(N0, 2 * G) >= 64) {
+    const size_t ncoef = ((size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 + 3) & ~(size_t)3;
+    const size_t sm2 = (ncoef + (size_t)cpow(N0, 2 * G) * kThreadsX) * sizeof(Tc);
+    auto kern = encode_pass_staged_kernel<Tin, Tc, N0, G, S>;
+    cudaError_t e = prep(kern, sm2);
+    if (e != cudaSuccess) return e;
+    kern<<<pass_grid(a_in.rows_out, a_in.cols_out, a_in.parents, 1), kThreadsX, sm2, st>>>(t, a_in);
+    return cudaGetLastError();
+  }
   constexpr int VEC = Vec<Tc, N0, G>::value;
   PassArgs a = a_in;
   a.vload = a.nb % VEC == 0 && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
@@ -569,11 +642,10 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 
 }  // namespace
 
-// Levels per pass: two for n0 = 2 (16 values per position); one for n0 = 3 and 4.  Passes
-// holding 64 or more values per position (three levels of n0 = 2, two of n0 = 3) need about
-// 220 registers, run at low occupancy, and measured slower than an extra pass over an
-// intermediate.
-int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
+// Levels per pass: up to three for n0 = 2, two for n0 = 3, one for n0 = 4.  Passes holding 64
+// or more values per position stage their input in shared memory (encode) or take one
+// position per thread (decode) to stay near 100 registers.
+int max_levels_per_pass(int n0) { return n0 == 2 ? 3 : (n0 == 3 ? 2 : 1); }
 
 size_t pass_smem_bytes(int R, int n0, int g, int es) { return (size_t)subtree_nodes(R, g) * R * n0 * n0 * es; }
 
