@@ -39,7 +39,7 @@ __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * c
 template <typename Tc, int N0, int G>
 struct Vec {
   static constexpr int n = cpow(N0, 2 * G);
-  static constexpr int value = n >= 64 ? 1 : (sizeof(Tc) == 8 && n >= 16 ? 2 : 4);
+  static constexpr int value = sizeof(Tc) == 8 ? (n >= 64 ? 1 : (n >= 16 ? 2 : 4)) : (n >= 64 ? 2 : 4);
 };
 
 template <typename T, int VEC>
@@ -75,21 +75,6 @@ __device__ __forceinline__ void store_vec(T* dst, const T (&x)[VEC]) {
     for (int v = 0; v < VEC; ++v) dst[v] = x[v];
   }
 }
-
-// Asynchronous global -> shared copy of one element (zero-filled when !pred; the source
-// address is then not read).
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc, bool pred) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  if constexpr (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gsrc), "r"(pred ? 4 : 0) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(pred ? 8 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Number of nodes of a G-level subtree with R children per node: sum_{j<G} R^j.
 __host__ __device__ inline int subtree_nodes(int R, int G) {
@@ -267,72 +252,6 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
         for (int v = 0; v < VEC; ++v) in[k * W + l][v] = (Tc)raw[v];
       }
     EncodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, in, emit);
-  }
-}
-
-// Deep encode pass (n0^(2G) >= 64 values per position): the CTA first copies the n0^G x n0^G
-// input row segments of its 128 positions into shared memory with coalesced loads, then each
-// thread forms the first level's children from shared memory and walks the remaining G-1
-// levels in registers.  This keeps the register count near that of a (G-1)-level pass.
-template <typename Tin, typename Tc, int N0, int G, int S>
-__global__ void __launch_bounds__(kThreadsX) encode_pass_staged_kernel(const __grid_constant__ Tables<Tc> t,
-                                                                       const PassArgs a) {
-  constexpr int W = cpow(N0, G), WC = W / N0;
-  using Tout = typename StoreType<S>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
-  const int ncoef = ((subtree_nodes(t.R, G) * t.R * N0 * N0) + 3) & ~3;
-  Tc* in_s = coef + ncoef;  // [W*W][kThreadsX]
-  const int tid = threadIdx.x;
-  const int64_t x0 = (int64_t)blockIdx.x * kThreadsX, x = x0 + tid;
-  const int64_t y = blockIdx.y;
-  const int64_t outs = a.outs_per_parent;
-  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
-    __syncthreads();
-    expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
-    const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
-    const bool ok = y < a.nb && x < a.nb;
-#pragma unroll 1
-    for (int blk = 0; blk < W * W; ++blk) {
-      const int k = blk / W, l = blk - k * W;
-      const Tin* src = ok ? X + (k * a.nb + y) * a.ldx + l * a.nb + x : X;
-      cp_async_elem<Tc>(&in_s[blk * kThreadsX + tid], reinterpret_cast<const Tc*>(src), ok);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    if (x >= a.cols_out) continue;
-    EncodeEmitV<Tc, S, 1> emit;
-    emit.Y = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
-    emit.strideY = a.strideY;
-    emit.off = y * a.ldy + x;
-    emit.kpanel = a.kpanel;
-    emit.split = a.split;
-    emit.vec = true;
-    emit.avail = 1;
-    const Tc* row = coef;  // root of the subtree: local id 0
-    const int R = t.R;
-    for (int r = 0; r < R; ++r) {
-      const Tc* c = row + r * (N0 * N0);
-      Tc cin[WC * WC][1];
-#pragma unroll
-      for (int e = 0; e < WC * WC; ++e) cin[e][0] = (Tc)0;
-#pragma unroll
-      for (int k = 0; k < N0; ++k)
-#pragma unroll
-        for (int l = 0; l < N0; ++l) {
-          const Tc cf = c[k * N0 + l];
-          if (cf != (Tc)0) {
-#pragma unroll
-            for (int u = 0; u < WC; ++u)
-#pragma unroll
-              for (int w = 0; w < WC; ++w)
-                cin[u * WC + w][0] =
-                    cin[u * WC + w][0] + cf * in_s[((k * WC + u) * W + (l * WC + w)) * kThreadsX + tid];
-          }
-        }
-      EncodeWalk<Tc, N0, G - 1, 1>::go(coef, R, 1, r, r, cin, emit);
-    }
   }
 }
 
@@ -528,80 +447,6 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
   }
 }
 
-// Deep decode pass (n0^(2G) >= 64 outputs per position): one position per thread; the
-// leaves under each top-level child r1 (R^(G-1) rows of the CTA's 128 positions) are copied
-// into a double-buffered shared tile with cp.async, the copies for r1 + 1 in flight while
-// r1's subtree is reduced, so that enough bytes stay in flight for HBM.
-template <typename Tm, typename To, typename Tc, int N0, int G>
-__global__ void __launch_bounds__(kThreadsX) decode_pass_staged_kernel(const __grid_constant__ Tables<Tc> t,
-                                                                       const PassArgs a) {
-  constexpr int W = cpow(N0, G), WC = W / N0;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
-  const int R = t.R;
-  const int ncoef = ((subtree_nodes(R, G) * R * N0 * N0) + 3) & ~3;
-  int sub = 1;  // leaves per top-level child: R^(G-1)
-  for (int j = 1; j < G; ++j) sub *= R;
-  Tm* buf = reinterpret_cast<Tm*>(coef + ncoef);  // [2][sub][kThreadsX]
-  const int tid = threadIdx.x;
-  const int64_t x = (int64_t)blockIdx.x * kThreadsX + tid;
-  const int64_t y = blockIdx.y;
-  const bool ok = x < a.nb && y < a.nb;
-  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
-    __syncthreads();
-    expand_subtree(t, a, G, 2, a.node_first + p, coef);
-    const Tm* M = static_cast<const Tm*>(a.X) + p * a.outs_per_parent * a.strideX;
-    const int64_t off = y * a.ldx + x;
-    auto issue = [&](int r1) {
-      Tm* dst = buf + (size_t)(r1 & 1) * sub * kThreadsX;
-#pragma unroll 1
-      for (int q = 0; q < sub; ++q) {
-        const Tm* src = ok ? M + (int64_t)(r1 * sub + q) * a.strideX + off : M;
-        cp_async_elem<Tm>(&dst[q * kThreadsX + tid], src, ok);
-      }
-      cp_async_commit();
-    };
-    issue(0);
-    Tc out[W * W][1];
-#pragma unroll
-    for (int e = 0; e < W * W; ++e) out[e][0] = (Tc)0;
-    for (int r1 = 0; r1 < R; ++r1) {
-      if (r1 + 1 < R) {
-        issue(r1 + 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      // each thread reads only its own column of the tile: no barrier needed
-      const Tm* tile = buf + (size_t)(r1 & 1) * sub * kThreadsX;
-      auto fetch = [&](int64_t path, Tc (&dst)[1]) { dst[0] = (Tc)tile[(path - (int64_t)r1 * sub) * kThreadsX + tid]; };
-      Tc cout[WC * WC][1];
-      DecodeWalk<Tc, N0, G - 1, 1>::go(coef, R, 1, r1, r1, cout, fetch);
-      const Tc* c = coef + r1 * (N0 * N0);  // root node, local id 0
-#pragma unroll
-      for (int i = 0; i < N0; ++i)
-#pragma unroll
-        for (int jj = 0; jj < N0; ++jj) {
-          const Tc wv = c[i * N0 + jj];
-          if (wv != (Tc)0) {
-#pragma unroll
-            for (int u = 0; u < WC; ++u)
-#pragma unroll
-              for (int w = 0; w < WC; ++w)
-                out[(i * WC + u) * W + (jj * WC + w)][0] =
-                    out[(i * WC + u) * W + (jj * WC + w)][0] + wv * cout[u * WC + w][0];
-          }
-        }
-    }
-    if (!ok) continue;
-    To* P = static_cast<To*>(a.Y) + p * a.strideY;
-#pragma unroll
-    for (int k = 0; k < W; ++k)
-#pragma unroll
-      for (int l = 0; l < W; ++l) P[(k * a.nb + y) * a.ldy + l * a.nb + x] = (To)out[k * W + l][0];
-  }
-}
-
 inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
   const int64_t span = (int64_t)kThreadsX * vec;
@@ -628,15 +473,6 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
     cudaError_t e = prep(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, block, smem, st>>>(t, a_in);
-    return cudaGetLastError();
-  }
-  if constexpr (cpow(N0, 2 * G) >= 64) {
-    const size_t ncoef = ((size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 + 3) & ~(size_t)3;
-    const size_t sm2 = (ncoef + (size_t)cpow(N0, 2 * G) * kThreadsX) * sizeof(Tc);
-    auto kern = encode_pass_staged_kernel<Tin, Tc, N0, G, S>;
-    cudaError_t e = prep(kern, sm2);
-    if (e != cudaSuccess) return e;
-    kern<<<pass_grid(a_in.rows_out, a_in.cols_out, a_in.parents, 1), kThreadsX, sm2, st>>>(t, a_in);
     return cudaGetLastError();
   }
   constexpr int VEC = Vec<Tc, N0, G>::value;
@@ -677,17 +513,6 @@ cudaError_t enc_n0(const Tables<Tc>& t, const PassArgs& a, int n0, int g, cudaSt
 
 template <typename Tm, typename To, typename Tc, int N0, int G>
 cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) {
-  if constexpr (cpow(N0, 2 * G) >= 64) {
-    int sub = 1;
-    for (int j = 1; j < G; ++j) sub *= t.R;
-    const size_t ncoef = ((size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 + 3) & ~(size_t)3;
-    const size_t sm2 = ncoef * sizeof(Tc) + 2 * (size_t)sub * kThreadsX * sizeof(Tm);
-    auto kern = decode_pass_staged_kernel<Tm, To, Tc, N0, G>;
-    cudaError_t e = prep(kern, sm2);
-    if (e != cudaSuccess) return e;
-    kern<<<pass_grid(a_in.nb, a_in.nb, a_in.parents, 1), kThreadsX, sm2, st>>>(t, a_in);
-    return cudaGetLastError();
-  }
   constexpr int VEC = Vec<Tc, N0, G>::value;
   const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
   PassArgs a = a_in;
@@ -744,10 +569,11 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 
 }  // namespace
 
-// Levels per pass: up to three for n0 = 2, two for n0 = 3, one for n0 = 4.  Passes holding 64
-// or more values per position stage their input in shared memory (encode) or take one
-// position per thread (decode) to stay near 100 registers.
-int max_levels_per_pass(int n0) { return n0 == 2 ? 3 : (n0 == 3 ? 2 : 1); }
+// Levels per pass: two for n0 = 2 (16 values per position); one for n0 = 3 and 4.  Passes
+// holding 64 or more values per position (three levels of n0 = 2, two of n0 = 3) need about
+// 220 registers, run at low occupancy, and measured slower than an extra pass over an
+// intermediate.
+int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
 
 size_t pass_smem_bytes(int R, int n0, int g, int es) { return (size_t)subtree_nodes(R, g) * R * n0 * n0 * es; }
 
