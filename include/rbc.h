@@ -194,6 +194,48 @@ rbc_status rbc_matmul_static(rbc_plan_t plan, const void* A, const void* B, void
                              void* stream);
 size_t rbc_static_scratch_bytes(void);
 
+/* Grouped batch of independent products with fp32 I/O and tensor-core leaves (many
+ * instances of uneven sizes, formulas, depths and seeds).  Each instance follows Section
+ * 2.1.1 exactly as rbc_matmul does (staged decode); the R^L leaf products of ALL instances
+ * run in one persistent tensor-core launch.  Items are copied at creation; their plans and
+ * device buffers must stay valid while the group is used.  A group is used by one host
+ * thread at a time. */
+typedef struct {
+  rbc_plan_t plan;
+  const void* A;   /* device, fp32, N x N, leading dimension lda */
+  const void* B;
+  void* C;         /* device, fp32, overwritten */
+  int64_t N, lda, ldb, ldc;
+} rbc_group_item;
+
+typedef struct rbc_group_s* rbc_group_t;
+
+/* Tile configuration chosen by rbc_group_tune: tile width bn (128 or 256), tile order group
+ * (0: per-instance default, 1: row-major, 8: groups of 8 tile rows), candidates timed and the
+ * best grouped-launch time in milliseconds. */
+typedef struct {
+  int bn, group, candidates;
+  float best_ms;
+} rbc_group_tuning;
+
+#define RBC_GROUP_GRAPH 1  /* rbc_group_run flag: capture once into a CUDA graph, then replay */
+
+/* Validate the items and lay out their workspaces.  A tuning found earlier in the process for
+ * the same signature (leaf mode and instance shapes) is reused.  Host only. */
+rbc_status rbc_group_create(const rbc_group_item* items, int count, int leaf_dtype, rbc_group_t* out);
+size_t rbc_group_workspace_size(rbc_group_t group);
+/* Enqueue the whole batch on `stream` (asynchronous).  With RBC_GROUP_GRAPH the first call
+ * captures the sequence into a CUDA graph (the workspace and stream are bound to it) and
+ * every call launches that graph.  The first call with a new workspace uploads the instance
+ * descriptors synchronously. */
+rbc_status rbc_group_run(rbc_group_t group, void* workspace, size_t workspace_bytes, void* stream, int flags);
+/* Autotuner: runs the batch once, then times the grouped leaf launch for every candidate tile
+ * configuration and keeps the fastest (also for later groups of the same signature).
+ * Synchronizes the stream.  `out` may be NULL. */
+rbc_status rbc_group_tune(rbc_group_t group, void* workspace, size_t workspace_bytes, void* stream,
+                          rbc_group_tuning* out);
+void rbc_group_destroy(rbc_group_t group);
+
 /* Device-side status of the calls that used `workspace` (its first 4 bytes, cleared by every
  * rbc_matmul): waits for `stream`, copies the word to *device_status and clears it.  0 means
  * no error; RBC_ETIMEOUT means a bounded wait inside a kernel expired and that kernel skipped

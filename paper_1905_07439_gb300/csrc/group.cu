@@ -1,0 +1,321 @@
+// Grouped batch of independent products C_i = F^(L_i)(A_i, B_i) (Section 2.1.1) with fp32
+// I/O and tensor-core leaves.  Each instance is encoded and decoded by its own passes; the
+// leaf products of all instances run in ONE persistent tcgen05 launch whose tile scheduler
+// walks a global tile list (instance-major, then leaf, then tile), reading each instance's
+// descriptor and TMA tensor maps from device memory.  The whole sequence can be captured
+// once into a CUDA graph and replayed; a small autotuner times the candidate tile widths and
+// tile orders of the grouped launch and keeps the fastest for the batch's signature.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "matmul_internal.h"
+#include "rbc_internal.h"
+#include "tc_gemm.cuh"
+
+using namespace rbc;
+using namespace rbc::detail;
+
+namespace {
+
+struct Config {
+  int bn = 128;
+  int group = 0;  // 0: per instance default, 1: row-major, 8: groups of 8 tile rows
+};
+
+std::mutex g_cache_mutex;
+std::map<std::string, Config> g_tuned;  // autotuner results by batch signature
+
+struct TablesHolder {
+  std::unique_ptr<Tables<float>> t{new Tables<float>()};
+};
+
+}  // namespace
+
+struct rbc_group_s {
+  int leaf = 0;
+  std::vector<rbc_group_item> items;
+  std::vector<Layout> layouts;
+  std::vector<size_t> ws_off;   // per-instance sub-workspace offsets
+  size_t inst_off = 0, maps_off = 0, total = 0;
+  bool bn256_ok = false;
+  Config cfg;
+  std::string signature;
+  // binding of the device-side descriptors to a workspace
+  void* bound_ws = nullptr;
+  Config bound_cfg;
+  int64_t total_tiles = 0;
+  // captured graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* graph_ws = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  ~rbc_group_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+namespace {
+
+TcGemmArgs inst_args(const rbc_group_s* g, size_t i, char* ws) {
+  const Layout& lo = g->layouts[i];
+  char* w = ws + g->ws_off[i];
+  TcGemmArgs a{};
+  a.S = w + lo.leafS;
+  a.T = w + lo.leafT;
+  a.K = lo.K;
+  a.m = lo.m;
+  a.mp = lo.mp;
+  a.leaves = ipow(g->items[i].plan->R, g->items[i].plan->L);
+  a.C = g->items[i].C;
+  a.ldc = g->items[i].ldc;
+  a.direct = g->items[i].plan->L == 0;
+  a.store_m = g->items[i].plan->L > 0;
+  a.M = w + lo.M;
+  a.leaf = g->leaf;
+  a.status = reinterpret_cast<int*>(ws);
+  return a;
+}
+
+// Write the instance descriptors and tensor maps for `cfg` into the workspace.
+rbc_status bind(rbc_group_s* g, char* ws, const Config& cfg) {
+  const size_t n = g->items.size();
+  std::vector<TcInst> insts(n);
+  std::vector<CUtensorMap> maps(2 * n);
+  int64_t tiles = 0;
+  for (size_t i = 0; i < n; ++i) {
+    TcGemmArgs a = inst_args(g, i, ws);
+    const int grp = cfg.group ? cfg.group : tc_default_group(g->leaf, a.mp, a.K);
+    if (!tc_prepare_instance(a, cfg.bn, grp, tiles, &insts[i], &maps[2 * i]))
+      return fail(RBC_EINVAL, "instance " + std::to_string(i) + ": tensor map or tile shape rejected");
+    tiles += tc_instance_tiles(insts[i]);
+  }
+  cudaError_t e = cudaMemcpy(ws + g->inst_off, insts.data(), n * sizeof(TcInst), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ws + g->maps_off, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  g->bound_ws = ws;
+  g->bound_cfg = cfg;
+  g->total_tiles = tiles;
+  return RBC_OK;
+}
+
+rbc_status grouped_gemm(rbc_group_s* g, char* ws, cudaStream_t st) {
+  TcGroupArgs ga{};
+  ga.insts = reinterpret_cast<const TcInst*>(ws + g->inst_off);
+  ga.maps = ws + g->maps_off;
+  ga.ninst = (int)g->items.size();
+  ga.total_tiles = g->total_tiles;
+  ga.leaf = g->leaf;
+  ga.bn = g->bound_cfg.bn;
+  ga.status = reinterpret_cast<int*>(ws);
+  cudaError_t e = launch_tc_gemm_grouped(ga, st);
+  ++g_launches;
+  return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+}
+
+// The whole batch on one stream: encodes, one grouped leaf launch, decodes.
+rbc_status enqueue(rbc_group_s* g, char* ws, cudaStream_t st) {
+  static thread_local TablesHolder holder;
+  Tables<float>& tab = *holder.t;
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);
+  if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  for (size_t i = 0; i < g->items.size(); ++i) {
+    const rbc_group_item& it = g->items[i];
+    char* w = ws + g->ws_off[i];
+    rbc_status s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 0, it.A, it.lda, w, tab, st);
+    if (s == RBC_OK) s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 1, it.B, it.ldb, w, tab, st);
+    if (s != RBC_OK) return s;
+  }
+  rbc_status s = grouped_gemm(g, ws, st);
+  if (s != RBC_OK) return s;
+  for (size_t i = 0; i < g->items.size(); ++i) {
+    const rbc_group_item& it = g->items[i];
+    if (it.plan->L == 0) continue;  // the leaf launch wrote C directly
+    s = decode_passes<float>(it.plan, g->layouts[i], it.C, it.ldc, ws + g->ws_off[i], tab, st);
+    if (s != RBC_OK) return s;
+  }
+  return RBC_OK;
+}
+
+rbc_status check_ws(const rbc_group_s* g, void* ws, size_t bytes) {
+  if (!ws || ((uintptr_t)ws & 255)) return fail(RBC_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (bytes < g->total) return fail(RBC_ENOMEM, "workspace too small");
+  return RBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rbc_status rbc_group_create(const rbc_group_item* items, int count, int leaf_dtype, rbc_group_t* out) {
+  if (!items || !out || count <= 0) return fail(RBC_EINVAL, "null argument or empty batch");
+  *out = nullptr;
+  if (!is_tc_leaf(leaf_dtype)) return fail(RBC_EUNSUPPORTED, "grouped batches use tensor-core leaf modes");
+  std::unique_ptr<rbc_group_s> g(new (std::nothrow) rbc_group_s());
+  if (!g) return fail(RBC_ENOMEM, "out of host memory");
+  g->leaf = leaf_dtype;
+  g->items.assign(items, items + count);
+  size_t off = kStatusBytes;
+  bool all256 = leaf_dtype != RBC_LEAF_3XBF16 && leaf_dtype != RBC_LEAF_3XTF32;
+  std::ostringstream sig;
+  sig << leaf_dtype;
+  for (int i = 0; i < count; ++i) {
+    const rbc_group_item& it = items[i];
+    if (!it.plan || !it.A || !it.B || !it.C) return fail(RBC_EINVAL, "null pointer in item " + std::to_string(i));
+    if (it.lda < it.N || it.ldb < it.N || it.ldc < it.N) return fail(RBC_EINVAL, "leading dimension below N");
+    Layout lo;
+    rbc_status s = make_layout(it.plan, it.N, RBC_IO_F32, leaf_dtype, 2, &lo);
+    if (s != RBC_OK) return s;
+    g->layouts.push_back(lo);
+    g->ws_off.push_back(off);
+    off = align256(off + lo.total);
+    all256 = all256 && lo.mp % 256 == 0;
+    sig << ';' << lo.mp << 'x' << ipow(it.plan->R, it.plan->L);
+  }
+  g->inst_off = off;
+  off = align256(off + (size_t)count * sizeof(TcInst));
+  g->maps_off = off;
+  off = align256(off + (size_t)count * 2 * sizeof(CUtensorMap));
+  g->total = off;
+  g->bn256_ok = all256;
+  g->signature = sig.str();
+  g->cfg.bn = 128;
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    auto f = g_tuned.find(g->signature);
+    if (f != g_tuned.end()) g->cfg = f->second;
+  }
+  *out = g.release();
+  return RBC_OK;
+}
+
+size_t rbc_group_workspace_size(rbc_group_t g) { return g ? g->total : 0; }
+
+rbc_status rbc_group_run(rbc_group_t g, void* workspace, size_t bytes, void* stream, int flags) {
+  if (!g) return fail(RBC_EINVAL, "null group");
+  rbc_status s = check_ws(g, workspace, bytes);
+  if (s != RBC_OK) return s;
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (g->bound_ws != ws || g->bound_cfg.bn != g->cfg.bn || g->bound_cfg.group != g->cfg.group) {
+    s = bind(g, ws, g->cfg);
+    if (s != RBC_OK) return s;
+    if (g->exec) {
+      cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+    }
+    if (g->graph) {
+      cudaGraphDestroy(g->graph);
+      g->graph = nullptr;
+    }
+  }
+  g_launches = 0;
+  if (!(flags & RBC_GROUP_GRAPH)) return enqueue(g, ws, st);
+  if (!g->exec || g->graph_ws != ws || g->graph_stream != st) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->exec = nullptr;
+    g->graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+    s = enqueue(g, ws, st);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (s != RBC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return fail(RBC_ECUDA, cudaGetErrorString(e));
+    }
+    g->graph = graph;
+    g->graph_ws = ws;
+    g->graph_stream = st;
+  }
+  cudaError_t e = cudaGraphLaunch(g->exec, st);
+  return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+}
+
+rbc_status rbc_group_tune(rbc_group_t g, void* workspace, size_t bytes, void* stream, rbc_group_tuning* out) {
+  if (!g) return fail(RBC_EINVAL, "null group");
+  rbc_status s = check_ws(g, workspace, bytes);
+  if (s != RBC_OK) return s;
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // leaf operands must exist once: run the batch eagerly with the current configuration
+  s = bind(g, ws, g->cfg);
+  if (s == RBC_OK) s = enqueue(g, ws, st);
+  if (s != RBC_OK) return s;
+  std::vector<Config> cands;
+  for (int bn : {128, 256}) {
+    if (bn == 256 && !g->bn256_ok) continue;
+    for (int grp : {0, 1, 8}) cands.push_back(Config{bn, grp});
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(RBC_ECUDA, "event creation failed");
+  float best_ms = 1e30f;
+  Config best = g->cfg;
+  int ntried = 0;
+  for (const Config& c : cands) {
+    s = bind(g, ws, c);
+    if (s != RBC_OK) break;
+    s = grouped_gemm(g, ws, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && s == RBC_OK; ++r) s = grouped_gemm(g, ws, st);
+    cudaEventRecord(e1, st);
+    if (s != RBC_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      s = fail(RBC_ECUDA, "tuning run failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.f;
+    ++ntried;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != RBC_OK) return s;
+  g->cfg = best;
+  s = bind(g, ws, best);
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  if (g->graph) {
+    cudaGraphDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    g_tuned[g->signature] = best;
+  }
+  if (out) {
+    out->bn = best.bn;
+    out->group = best.group;
+    out->candidates = ntried;
+    out->best_ms = best_ms;
+  }
+  return s;
+}
+
+void rbc_group_destroy(rbc_group_t g) { delete g; }
+
+}  // extern "C"

@@ -9,19 +9,15 @@
 
 #include "convert.cuh"
 #include "level_kernels.cuh"
+#include "matmul_internal.h"
 #include "rbc_internal.h"
 #include "tc_gemm.cuh"
 
 namespace rbc {
-namespace {
+namespace detail {
 
 thread_local int64_t g_launches = 0;  // kernels launched by the current call
 
-constexpr size_t kStatusBytes = 256;
-
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-// Leading dimension of an intermediate operand: rows start 16-byte aligned for vector access.
-inline int64_t pad_ld(int64_t n) { return (n + 3) / 4 * 4; }
 
 bool is_tc_leaf(int leaf) {
   return leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_BF16 || leaf == RBC_LEAF_F16 ||
@@ -43,15 +39,6 @@ int leaf_store(int leaf) {
 
 size_t store_bytes(int s) { return s == kStoreF64 ? 8 : (s == kStoreBF16 || s == kStoreF16) ? 2 : 4; }
 
-// Grouping of the L levels into passes, root first: [L - (k-1)*g, g, ..., g] with g the most
-// levels one pass holds in registers; the small pass sits at the root, where intermediates
-// are smallest ((R/n0^2)^depth N^2 elements).
-struct Passes {
-  int count = 0;
-  int g[kMaxLevels] = {};
-  int top[kMaxLevels] = {};  // depth of the parents of each pass
-};
-
 Passes plan_passes(int L, int n0) {
   Passes ps;
   if (L == 0) return ps;
@@ -66,16 +53,6 @@ Passes plan_passes(int L, int n0) {
   ps.count = k;
   return ps;
 }
-
-struct Layout {
-  int64_t m = 0, mp = 0, K = 0;
-  int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 staged passes
-  size_t es_io = 0, es_acc = 0, es_leaf = 0;
-  Passes passes;
-  size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
-  size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
-  size_t total = 0;
-};
 
 // Contributions per C element of the fused decode: (sum_r nnz(W_::r) / n0^2)^L.
 double fused_contributions(const rbc_plan_s* p) {
@@ -393,10 +370,16 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
   return RBC_OK;
 }
 
-}  // namespace
+template rbc_status encode_operand<float>(const rbc_plan_s*, const Layout&, int, int, const void*, int64_t, char*,
+                                          Tables<float>&, cudaStream_t);
+template rbc_status decode_passes<float>(const rbc_plan_s*, const Layout&, void*, int64_t, char*, Tables<float>&,
+                                         cudaStream_t);
+
+}  // namespace detail
 }  // namespace rbc
 
 using namespace rbc;
+using namespace rbc::detail;
 
 extern "C" {
 

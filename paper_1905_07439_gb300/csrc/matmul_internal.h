@@ -1,0 +1,53 @@
+// Pieces of rbc_matmul shared with the grouped batch: workspace layout and the encode /
+// decode pass sequences of one product.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rbc_internal.h"
+
+namespace rbc {
+namespace detail {
+
+constexpr size_t kStatusBytes = 256;  // device status word(s) at the start of a workspace
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+// Leading dimension of an intermediate operand: rows start 16-byte aligned for vector access.
+inline int64_t pad_ld(int64_t n) { return (n + 3) / 4 * 4; }
+
+extern thread_local int64_t g_launches;
+
+// Grouping of the L levels into passes, root first: [L - (k-1)*g, g, ..., g] with g the most
+// levels one pass holds in registers; the small pass sits at the root, where intermediates
+// are smallest ((R/n0^2)^depth N^2 elements).
+struct Passes {
+  int count = 0;
+  int g[kMaxLevels] = {};
+  int top[kMaxLevels] = {};  // depth of the parents of each pass
+};
+
+struct Layout {
+  int64_t m = 0, mp = 0, K = 0;
+  int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 staged passes
+  size_t es_io = 0, es_acc = 0, es_leaf = 0;
+  Passes passes;
+  size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
+  size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
+  size_t total = 0;
+};
+
+bool is_tc_leaf(int leaf);
+Passes plan_passes(int L, int n0);
+rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo);
+
+template <typename T>
+rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
+                          int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st);
+template <typename T>
+rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
+                         Tables<T>& tab, cudaStream_t st);
+
+}  // namespace detail
+}  // namespace rbc

@@ -36,18 +36,30 @@ constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct Params {
-  int64_t m, mp, leaves, total_tiles;
-  int nk, tiles_m, tiles_n, group_m;
-  int kpanel;      // element offset of the lo panel along K (split modes)
+  TcInst one;                 // the instance of a single product
+  const TcInst* insts;        // grouped launches: device array of ninst instances
+  const CUtensorMap* maps;    // grouped launches: tensor maps, (S, T) per instance
+  int ninst;
+  int64_t total_tiles;
   uint32_t idesc;
-  int epi;         // 0: fused decode by reductions, 1: direct store (L = 0), 2: store M
-  int vec_ok;      // 16-byte vector access to C allowed
-  float* C;
-  int64_t ldc;
-  float* M;
-  int64_t ldm, strideM;
   int* status;
 };
+
+// Instance owning global tile `tile`: the last one whose tile_begin <= tile.
+template <bool GROUPED>
+__device__ __forceinline__ int find_inst(const Params& p, int64_t tile) {
+  if constexpr (!GROUPED) {
+    return 0;
+  } else {
+    int lo = 0, hi = p.ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.insts[mid].tile_begin <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
+}
 
 template <int STAGES>
 struct Aux {
@@ -70,7 +82,7 @@ __device__ __forceinline__ void raise_abort(volatile int* abort, int* status) {
 // that the CTAs running at the same time share A row panels and B column panels in L2 (a
 // plain row-major order re-streams every B panel from DRAM once per tile row when a leaf's
 // operands exceed L2).  group_m = 1 is the row-major order.
-__device__ __forceinline__ void tile_coords(int64_t tile, const Params& p, int64_t* leaf, int* tm, int* tn) {
+__device__ __forceinline__ void tile_coords(int64_t tile, const TcInst& p, int64_t* leaf, int* tm, int* tn) {
   const int64_t per_leaf = (int64_t)p.tiles_m * p.tiles_n;
   *leaf = tile / per_leaf;
   const int r = (int)(tile - *leaf * per_leaf);
@@ -83,7 +95,7 @@ __device__ __forceinline__ void tile_coords(int64_t tile, const Params& p, int64
   *tn = w / gm;
 }
 
-template <int KIND, int SPLIT, int BN, int STAGES>
+template <int KIND, int SPLIT, int BN, int STAGES, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ Tables<float> t, const Params p) {
@@ -117,8 +129,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::mbar_init(&aux->drain, 1);
     aux->abort = 0;
     ptx::fence_mbar_init();
-    ptx::prefetch_tmap(&tmA);
-    ptx::prefetch_tmap(&tmB);
+    if (!GROUPED) {
+      ptx::prefetch_tmap(&tmA);
+      ptx::prefetch_tmap(&tmB);
+    }
   }
   if (warp == 1) {
     ptx::tmem_alloc(&aux->tmem_base, 2 * BN);
@@ -135,13 +149,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       int s = 0;
       uint32_t ph = 0;
       uint32_t armed = 0, last_par = 0;  // per-stage bit masks for the teardown drain
+      int fenced = -1;                   // grouped: instance whose maps were last fenced
       for (int64_t tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+        const int ii = find_inst<GROUPED>(p, tile);
+        const TcInst d = GROUPED ? p.insts[ii] : p.one;
+        const void* mA = GROUPED ? (const void*)&p.maps[2 * ii] : (const void*)&tmA;
+        const void* mB = GROUPED ? (const void*)&p.maps[2 * ii + 1] : (const void*)&tmB;
+        if (GROUPED && ii != fenced) {
+          ptx::fence_tmap_acquire(mA);
+          ptx::fence_tmap_acquire(mB);
+          fenced = ii;
+        }
         int64_t leaf;
         int tm, tn;
-        tile_coords(tile, p, &leaf, &tm, &tn);
-        const int32_t rowA = (int32_t)(leaf * p.mp + (int64_t)tm * BM);
+        tile_coords(tile - d.tile_begin, d, &leaf, &tm, &tn);
+        const int32_t rowA = (int32_t)(leaf * d.mp + (int64_t)tm * BM);
         const int32_t colB = tn * BN;
-        for (int kb = 0; kb < p.nk; ++kb) {
+        for (int kb = 0; kb < d.nk; ++kb) {
           if (!ptx::wait_bounded(&aux->empty[s], ph ^ 1u, abort, kWaitNs)) {
             raise_abort(abort, p.status);
             break;
@@ -149,22 +173,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* st = smem + s * STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&aux->full[s], STAGE_BYTES);
           const int32_t kx = kb * KELEM;
-          ptx::tma_load_2d(st, &tmA, &aux->full[s], kx, rowA);
-          if (SPLIT) ptx::tma_load_2d(st + A_BYTES, &tmA, &aux->full[s], kx + p.kpanel, rowA);
+          ptx::tma_load_2d(st, mA, &aux->full[s], kx, rowA);
+          if (SPLIT) ptx::tma_load_2d(st + A_BYTES, mA, &aux->full[s], kx + d.kpanel, rowA);
           if constexpr (BMN) {
-            const int32_t rowB = (int32_t)(leaf * p.mp) + kx;
+            const int32_t rowB = (int32_t)(leaf * d.mp) + kx;
             constexpr int NBOX = kRowBytes / (KIND == 0 ? 2 : 4);
 #pragma unroll
             for (int j = 0; j < B_BOXES; ++j) {
-              ptx::tma_load_2d(st + P * A_BYTES + j * B_ATOM, &tmB, &aux->full[s], colB + j * NBOX, rowB);
+              ptx::tma_load_2d(st + P * A_BYTES + j * B_ATOM, mB, &aux->full[s], colB + j * NBOX, rowB);
               if (SPLIT)
-                ptx::tma_load_2d(st + P * A_BYTES + B_BYTES + j * B_ATOM, &tmB, &aux->full[s],
-                                 colB + j * NBOX + p.kpanel, rowB);
+                ptx::tma_load_2d(st + P * A_BYTES + B_BYTES + j * B_ATOM, mB, &aux->full[s],
+                                 colB + j * NBOX + d.kpanel, rowB);
             }
           } else {
-            const int32_t rowB = (int32_t)(leaf * p.mp) + colB;
-            ptx::tma_load_2d(st + P * A_BYTES, &tmB, &aux->full[s], kx, rowB);
-            if (SPLIT) ptx::tma_load_2d(st + P * A_BYTES + B_BYTES, &tmB, &aux->full[s], kx + p.kpanel, rowB);
+            const int32_t rowB = (int32_t)(leaf * d.mp) + colB;
+            ptx::tma_load_2d(st + P * A_BYTES, mB, &aux->full[s], kx, rowB);
+            if (SPLIT) ptx::tma_load_2d(st + P * A_BYTES + B_BYTES, mB, &aux->full[s], kx + d.kpanel, rowB);
           }
           armed |= 1u << s;
           last_par = (last_par & ~(1u << s)) | (ph << s);
@@ -193,8 +217,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        const int nk = GROUPED ? p.insts[find_inst<GROUPED>(p, tile)].nk : p.one.nk;
         bool ok = true;
-        for (int kb = 0; kb < p.nk; ++kb) {
+        for (int kb = 0; kb < nk; ++kb) {
           if (!ptx::wait_bounded(&aux->full[s], ph, abort, kWaitNs)) {
             raise_abort(abort, p.status);
             ok = false;
@@ -245,11 +270,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     int buf = 0;
     uint32_t aph = 0;
     for (int64_t tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x) {
+      const TcInst d = GROUPED ? p.insts[find_inst<GROUPED>(p, tile)] : p.one;
       int64_t leaf;
       int tm, tn;
-      tile_coords(tile, p, &leaf, &tm, &tn);
+      tile_coords(tile - d.tile_begin, d, &leaf, &tm, &tn);
       __syncwarp();  // every lane is done with the previous tile's list
-      if (p.epi == 0 && lane == 0) build_dest_list(t, leaf, dl);
+      if (d.epi == 0 && lane == 0) build_dest_list(t, leaf, dl);
       int ok = 1;
       if (lane == 0) ok = ptx::wait_bounded(&aux->tfull[buf], aph, abort, kWaitNs) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -271,35 +297,35 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) ptx::mbar_arrive(&aux->tempty[buf]);
         }
         const int64_t col0 = (int64_t)tn * BN + c0;
-        if (p.epi == 2) {
-          float* dst = p.M + leaf * p.strideM + row * p.ldm + col0;
+        if (d.epi == 2) {
+          float* dst = d.M + leaf * d.strideM + row * d.ldm + col0;
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
           continue;
         }
-        if (row >= p.m) continue;
-        if (p.epi == 1) {
-          float* dst = p.C + row * p.ldc + col0;
+        if (row >= d.m) continue;
+        if (d.epi == 1) {
+          float* dst = d.C + row * d.ldc + col0;
 #pragma unroll
           for (int q = 0; q < 32; ++q)
-            if (col0 + q < p.m) dst[q] = v[q];
+            if (col0 + q < d.m) dst[q] = v[q];
           continue;
         }
-        for (int d = 0; d < dl.total; ++d) {
+        for (int di = 0; di < dl.total; ++di) {
           int64_t I, J;
-          const float coef = dest_at(dl, d, t.n0, t.L, &I, &J);
-          float* dst = p.C + (I * p.m + row) * p.ldc + J * p.m + col0;
+          const float coef = dest_at(dl, di, t.n0, t.L, &I, &J);
+          float* dst = d.C + (I * d.m + row) * d.ldc + J * d.m + col0;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int64_t c = col0 + 4 * q;
-            if (p.vec_ok && c + 3 < p.m) {
+            if (d.vec_ok && c + 3 < d.m) {
               ptx::red_add_v4(dst + 4 * q, coef * v[4 * q], coef * v[4 * q + 1], coef * v[4 * q + 2],
                               coef * v[4 * q + 3]);
             } else {
 #pragma unroll
               for (int e = 0; e < 4; ++e)
-                if (c + e < p.m) atomicAdd(dst + 4 * q + e, coef * v[4 * q + e]);
+                if (c + e < d.m) atomicAdd(dst + 4 * q + e, coef * v[4 * q + e]);
             }
           }
         }
@@ -347,21 +373,56 @@ bool make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int es
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KIND, int SPLIT, int BN, int STAGES>
+template <int KIND, int SPLIT, int BN, int STAGES, bool GROUPED>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t, const Params& p,
                    cudaStream_t st) {
   constexpr int P = SPLIT ? 2 : 1;
   constexpr size_t smem = (size_t)STAGES * P * (BM + BN) * kRowBytes + sizeof(Aux<STAGES>) + 1024;
   static_assert(smem <= 232448, "shared memory budget");
-  auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES>;
-  const cudaError_t attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (attr_err != cudaSuccess) return attr_err;
+  auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES, GROUPED>;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
+  // Once per device (never inside a later stream capture): allow the large shared memory.
+  static std::mutex mu;
+  static bool attr_set[64] = {};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+      const cudaError_t attr_err =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (attr_err != cudaSuccess) return attr_err;
+      attr_set[dev] = true;
+    }
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = p.total_tiles < sms ? p.total_tiles : sms;
+  if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(ma, mb, t, p);
   return cudaGetLastError();
+}
+
+// Kernel variant for a leaf mode and tile width.
+template <bool GROUPED>
+cudaError_t dispatch(int leaf, int bn, const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t,
+                     const Params& p, cudaStream_t st) {
+  const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
+  const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;
+  if (split && bn != 128) return cudaErrorInvalidValue;
+  if (tf32) {
+    if (split) return launch<1, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+    if (bn == 256) return launch<1, 0, 256, 4, GROUPED>(ma, mb, t, p, st);
+    return launch<1, 0, 128, 6, GROUPED>(ma, mb, t, p, st);
+  }
+  if (split) return launch<0, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+  if (bn == 256) return launch<0, 0, 256, 4, GROUPED>(ma, mb, t, p, st);
+  return launch<0, 0, 128, 6, GROUPED>(ma, mb, t, p, st);
+}
+
+uint32_t leaf_idesc(int leaf, int bn) {
+  const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
+  const uint32_t fmt = tf32 ? 2u : (leaf == RBC_LEAF_F16 ? 0u : 1u);
+  return ptx::idesc(fmt, fmt, BM, bn, tf32 ? 0u : 1u);
 }
 
 }  // namespace
@@ -369,54 +430,79 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<fl
 int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
 bool tc_supports_store_m() { return true; }
 
-cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStream_t st) {
+int tc_default_bn(int leaf, int64_t mp) {
+  const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;
+  return (!split && mp % 256 == 0) ? 256 : 128;
+}
+
+int tc_default_group(int leaf, int64_t mp, int64_t K) {
+  const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
+  const double leaf_bytes = 2.0 * (double)mp * (double)K * (tf32 ? 4 : 2);
+  // group tile rows only when one leaf's operands do not fit in L2 (about 64 MB per die)
+  return leaf_bytes > 64.0 * (1 << 20) ? 8 : 1;
+}
+
+bool tc_prepare_instance(const TcGemmArgs& a, int bn, int group_m, int64_t tile_begin, TcInst* d, void* maps2) {
   const bool tf32 = a.leaf == RBC_LEAF_TF32 || a.leaf == RBC_LEAF_3XTF32;
-  const bool split = a.leaf == RBC_LEAF_3XTF32 || a.leaf == RBC_LEAF_3XBF16;
   const int es = tf32 ? 4 : 2;
   const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                       : (a.leaf == RBC_LEAF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
-  const int bn = (!split && a.mp % 256 == 0) ? 256 : 128;
-  if (a.mp % 128 || a.mp % bn) return cudaErrorInvalidValue;
+  if (a.mp % 128 || a.mp % bn) return false;
   const int64_t rows = a.leaves * a.mp;
-  if (rows > INT32_MAX || a.K > INT32_MAX) return cudaErrorInvalidValue;
-  CUtensorMap ma, mb;
-  // A: rows of S (K contiguous), boxes 128 rows x 128 B.  B: rows of T are k, n contiguous;
-  // boxes of (K elements per stage) rows x 128 B of n.
-  if (!make_map(&ma, a.S, dt, es, a.K, rows, BM) ||
-      !make_map(&mb, a.T, dt, es, a.K, rows, tf32 ? bn : kRowBytes / es))
-    return cudaErrorInvalidValue;
+  if (rows > INT32_MAX || a.K > INT32_MAX) return false;
+  CUtensorMap* m = static_cast<CUtensorMap*>(maps2);
+  // A: rows of S (K contiguous), boxes 128 rows x 128 B.  B: T^T rows (tf32) like A, or T rows
+  // (k, n contiguous) in boxes of (K elements per stage) rows x 128 B of n.
+  if (!make_map(&m[0], a.S, dt, es, a.K, rows, BM) ||
+      !make_map(&m[1], a.T, dt, es, a.K, rows, tf32 ? bn : kRowBytes / es))
+    return false;
+  TcInst x{};
+  x.m = a.m;
+  x.mp = a.mp;
+  x.leaves = a.leaves;
+  x.tile_begin = tile_begin;
+  x.tiles_m = (int)(a.mp / BM);
+  x.tiles_n = (int)(a.mp / bn);
+  x.group_m = group_m;
+  x.nk = (int)(a.mp / (kRowBytes / es));
+  x.kpanel = (int)a.mp;
+  x.epi = a.store_m ? 2 : (a.direct ? 1 : 0);
+  x.vec_ok = ((uintptr_t)a.C % 16 == 0) && a.ldc % 4 == 0 && a.m % 4 == 0;
+  x.C = static_cast<float*>(a.C);
+  x.ldc = a.ldc;
+  x.M = static_cast<float*>(a.M);
+  x.ldm = a.mp;
+  x.strideM = a.mp * a.mp;
+  *d = x;
+  return true;
+}
+
+int64_t tc_instance_tiles(const TcInst& d) { return d.leaves * d.tiles_m * d.tiles_n; }
+
+cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStream_t st) {
+  const int bn = tc_default_bn(a.leaf, a.mp);
+  CUtensorMap maps[2];
   Params p{};
-  p.m = a.m;
-  p.mp = a.mp;
-  p.leaves = a.leaves;
-  p.tiles_m = (int)(a.mp / BM);
-  p.tiles_n = (int)(a.mp / bn);
-  p.total_tiles = a.leaves * p.tiles_m * p.tiles_n;
-  // group tile rows only when one leaf's operands do not fit in L2 (about 64 MB per die)
-  const double leaf_bytes = 2.0 * (double)a.mp * (double)a.K * es;
-  p.group_m = leaf_bytes > 64.0 * (1 << 20) ? 8 : 1;
-  const int kelem = kRowBytes / es;
-  p.nk = (int)(a.mp / kelem);
-  p.kpanel = (int)a.mp;
-  const uint32_t fmt = tf32 ? 2u : (a.leaf == RBC_LEAF_F16 ? 0u : 1u);
-  p.idesc = ptx::idesc(fmt, fmt, BM, bn, tf32 ? 0u : 1u);
-  p.epi = a.store_m ? 2 : (a.direct ? 1 : 0);
-  p.C = static_cast<float*>(a.C);
-  p.ldc = a.ldc;
-  p.vec_ok = ((uintptr_t)a.C % 16 == 0) && a.ldc % 4 == 0 && a.m % 4 == 0;
-  p.M = static_cast<float*>(a.M);
-  p.ldm = a.mp;
-  p.strideM = a.mp * a.mp;
+  if (!tc_prepare_instance(a, bn, tc_default_group(a.leaf, a.mp, a.K), 0, &p.one, maps))
+    return cudaErrorInvalidValue;
+  p.total_tiles = tc_instance_tiles(p.one);
+  p.idesc = leaf_idesc(a.leaf, bn);
   p.status = a.status;
-  if (tf32) {
-    if (split) return launch<1, 1, 128, 3>(ma, mb, t, p, st);
-    if (bn == 256) return launch<1, 0, 256, 4>(ma, mb, t, p, st);
-    return launch<1, 0, 128, 6>(ma, mb, t, p, st);
-  }
-  if (split) return launch<0, 1, 128, 3>(ma, mb, t, p, st);
-  if (bn == 256) return launch<0, 0, 256, 4>(ma, mb, t, p, st);
-  return launch<0, 0, 128, 6>(ma, mb, t, p, st);
+  return dispatch<false>(a.leaf, bn, maps[0], maps[1], t, p, st);
+}
+
+cudaError_t launch_tc_gemm_grouped(const TcGroupArgs& g, cudaStream_t st) {
+  static const Tables<float> kNoTables{};  // grouped launches store the leaf products (no fused decode)
+  Params p{};
+  p.insts = g.insts;
+  p.maps = static_cast<const CUtensorMap*>(g.maps);
+  p.ninst = g.ninst;
+  p.total_tiles = g.total_tiles;
+  p.idesc = leaf_idesc(g.leaf, g.bn);
+  p.status = g.status;
+  CUtensorMap unused{};
+  return dispatch<true>(g.leaf, g.bn, unused, unused, kNoTables, p, st);
 }
 
 }  // namespace rbc

@@ -24,8 +24,40 @@ struct TcGemmArgs {
   int* status;     // device status word (RBC_ETIMEOUT on an expired wait)
 };
 
+// One instance of a (possibly grouped) leaf-product launch, as the kernel reads it.
+struct TcInst {
+  int64_t m, mp, leaves, tile_begin;  // tile_begin: first global tile of this instance
+  int nk, tiles_m, tiles_n, group_m, kpanel;
+  int epi;     // 0: fused decode by reductions, 1: direct store (L = 0), 2: store M
+  int vec_ok;  // 16-byte vector access to C allowed
+  int pad_;
+  float* C;
+  int64_t ldc;
+  float* M;
+  int64_t ldm, strideM;
+};
+
+// A grouped launch: the leaf products of many instances (same leaf mode and tile width) in
+// one persistent kernel.  insts and maps live in device memory; maps holds two 64-byte
+// tensor maps (S, T) per instance.
+struct TcGroupArgs {
+  const TcInst* insts;
+  const void* maps;
+  int ninst;
+  int64_t total_tiles;
+  int leaf;
+  int bn;
+  int* status;
+};
+
 int64_t tc_pad(int64_t m);
 bool tc_supports_store_m();
+int tc_default_bn(int leaf, int64_t mp);
+int tc_default_group(int leaf, int64_t mp, int64_t K);
+// Fill the descriptor and the two tensor maps (host memory, 128 bytes) of one instance.
+bool tc_prepare_instance(const TcGemmArgs& a, int bn, int group_m, int64_t tile_begin, TcInst* d, void* maps2);
+int64_t tc_instance_tiles(const TcInst& d);
 cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStream_t st);
+cudaError_t launch_tc_gemm_grouped(const TcGroupArgs& g, cudaStream_t st);
 
 }  // namespace rbc

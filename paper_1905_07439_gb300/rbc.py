@@ -36,6 +36,18 @@ class rbc_plan_info(C.Structure):
                 ("scale", C.c_double), ("seed", C.c_uint64)]
 
 
+class rbc_group_item(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("A", C.c_void_p), ("B", C.c_void_p), ("C", C.c_void_p),
+                ("N", C.c_int64), ("lda", C.c_int64), ("ldb", C.c_int64), ("ldc", C.c_int64)]
+
+
+class rbc_group_tuning(C.Structure):
+    _fields_ = [("bn", C.c_int), ("group", C.c_int), ("candidates", C.c_int), ("best_ms", C.c_float)]
+
+
+RBC_GROUP_GRAPH = 1
+
+
 class rbc_matmul_opts(C.Structure):
     _fields_ = [("decode", C.c_int), ("reserved", C.c_int * 7), ("events", C.c_void_p * 4),
                 ("launches", C.c_int64)]
@@ -57,6 +69,11 @@ SIGNATURES = {
     "rbc_matmul_ex": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
                                 _P, C.c_size_t, _P, C.POINTER(rbc_matmul_opts)]),
     "rbc_workspace_check": (C.c_int, [_P, _P, C.POINTER(C.c_int)]),
+    "rbc_group_create": (C.c_int, [C.POINTER(rbc_group_item), C.c_int, C.c_int, C.POINTER(_P)]),
+    "rbc_group_workspace_size": (C.c_size_t, [_P]),
+    "rbc_group_run": (C.c_int, [_P, _P, C.c_size_t, _P, C.c_int]),
+    "rbc_group_tune": (C.c_int, [_P, _P, C.c_size_t, _P, C.POINTER(rbc_group_tuning)]),
+    "rbc_group_destroy": (None, [_P]),
     "rbc_matmul_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int,
                                     C.c_int, _P]),
     "rbc_static_scratch_bytes": (C.c_size_t, []),
@@ -214,3 +231,37 @@ def norms(X, Y=None, stream=None, work=None, out=None):
                           out.data_ptr(), work.data_ptr(), work.numel(), _stream_ptr(stream)),
           "rbc_norms")
     return out
+
+
+class Group:
+    """Owner of an rbc_group_t: a batch of products whose leaf products share one launch."""
+
+    def __init__(self, plans, As, Bs, Cs, leaf: int):
+        self.items = (rbc_group_item * len(plans))()
+        for i, (p, A, B, Cm) in enumerate(zip(plans, As, Bs, Cs)):
+            N = A.shape[0]
+            self.items[i] = rbc_group_item(p.handle.value, A.data_ptr(), B.data_ptr(), Cm.data_ptr(), N,
+                                           A.stride(0), B.stride(0), Cm.stride(0))
+        self._keep = (list(plans), list(As), list(Bs), list(Cs))
+        h = _P()
+        check(lib().rbc_group_create(self.items, len(plans), leaf, C.byref(h)), "rbc_group_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib().rbc_group_destroy(h)
+            self.handle = None
+
+    def workspace_size(self) -> int:
+        return int(lib().rbc_group_workspace_size(self.handle))
+
+    def run(self, workspace, stream=None, graph: bool = False):
+        check(lib().rbc_group_run(self.handle, workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
+                                  RBC_GROUP_GRAPH if graph else 0), "rbc_group_run")
+
+    def tune(self, workspace, stream=None) -> dict:
+        t = rbc_group_tuning()
+        check(lib().rbc_group_tune(self.handle, workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
+                                   C.byref(t)), "rbc_group_tune")
+        return {"bn": t.bn, "group": t.group, "candidates": t.candidates, "best_ms": t.best_ms}
