@@ -226,7 +226,8 @@ rbc_status rbc_group_create(const rbc_group_item* items, int count, int leaf_dty
 size_t rbc_group_workspace_size(rbc_group_t group);
 /* Enqueue the whole batch on `stream` (asynchronous).  With RBC_GROUP_GRAPH the first call
  * captures the sequence into a CUDA graph (the workspace and stream are bound to it) and
- * every call launches that graph.  The first call with a new workspace uploads the instance
+ * every call launches that graph; capture needs a created stream (RBC_EINVAL on the
+ * default stream).  The first call with a new workspace uploads the instance
  * descriptors synchronously. */
 rbc_status rbc_group_run(rbc_group_t group, void* workspace, size_t workspace_bytes, void* stream, int flags);
 /* Autotuner: runs the batch once, then times the grouped leaf launch for every candidate tile

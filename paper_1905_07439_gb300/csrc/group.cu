@@ -220,6 +220,8 @@ rbc_status rbc_group_run(rbc_group_t g, void* workspace, size_t bytes, void* str
   }
   g_launches = 0;
   if (!(flags & RBC_GROUP_GRAPH)) return enqueue(g, ws, st);
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+    return fail(RBC_EINVAL, "graph capture needs a created (non-default) stream");
   if (!g->exec || g->graph_ws != ws || g->graph_stream != st) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);

@@ -257,6 +257,17 @@ class Group:
         return int(lib().rbc_group_workspace_size(self.handle))
 
     def run(self, workspace, stream=None, graph: bool = False):
+        import torch
+        if graph and stream is None:
+            # graphs are captured on a created stream: run on a side stream ordered after and
+            # before the caller's current stream
+            cur = torch.cuda.current_stream()
+            if getattr(self, "_side", None) is None:
+                self._side = torch.cuda.Stream()
+            self._side.wait_stream(cur)
+            self.run(workspace, stream=self._side, graph=True)
+            cur.wait_stream(self._side)
+            return
         check(lib().rbc_group_run(self.handle, workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
                                   RBC_GROUP_GRAPH if graph else 0), "rbc_group_run")
 
