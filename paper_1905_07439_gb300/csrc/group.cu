@@ -57,9 +57,14 @@ struct rbc_group_s {
   cudaGraphExec_t exec = nullptr;
   void* graph_ws = nullptr;
   cudaStream_t graph_stream = nullptr;
+  // side streams and events for running instances' passes concurrently (fork / join)
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
   ~rbc_group_s() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    for (cudaStream_t s : side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
 };
 
@@ -122,28 +127,69 @@ rbc_status grouped_gemm(rbc_group_s* g, char* ws, cudaStream_t st) {
   return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
 }
 
-// The whole batch on one stream: encodes, one grouped leaf launch, decodes.
+constexpr int kSideStreams = 8;
+
+rbc_status ensure_side(rbc_group_s* g) {
+  if (!g->side.empty()) return RBC_OK;
+  for (int i = 0; i < kSideStreams; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(RBC_ECUDA, "stream creation failed");
+    g->side.push_back(s);
+  }
+  for (int i = 0; i < 2 * kSideStreams + 2; ++i) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(RBC_ECUDA, "event creation failed");
+    g->ev.push_back(e);
+  }
+  return RBC_OK;
+}
+
+// Fork: every side stream waits for `st`; join: `st` waits for every side stream.
+rbc_status fork(rbc_group_s* g, cudaStream_t st, cudaEvent_t e) {
+  if (cudaEventRecord(e, st) != cudaSuccess) return fail(RBC_ECUDA, "event record failed");
+  for (cudaStream_t s : g->side)
+    if (cudaStreamWaitEvent(s, e, 0) != cudaSuccess) return fail(RBC_ECUDA, "stream wait failed");
+  return RBC_OK;
+}
+rbc_status join(rbc_group_s* g, cudaStream_t st, const cudaEvent_t* evs) {
+  for (size_t i = 0; i < g->side.size(); ++i) {
+    if (cudaEventRecord(evs[i], g->side[i]) != cudaSuccess) return fail(RBC_ECUDA, "event record failed");
+    if (cudaStreamWaitEvent(st, evs[i], 0) != cudaSuccess) return fail(RBC_ECUDA, "stream wait failed");
+  }
+  return RBC_OK;
+}
+
+// The whole batch: the instances' encodes spread over the side streams, one grouped leaf
+// launch on `st`, then the decodes spread again; ordered on `st` before and after.
 rbc_status enqueue(rbc_group_s* g, char* ws, cudaStream_t st) {
   static thread_local TablesHolder holder;
   Tables<float>& tab = *holder.t;
+  rbc_status s = ensure_side(g);
+  if (s != RBC_OK) return s;
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);
   if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  const int ns = (int)g->side.size();
+  if ((s = fork(g, st, g->ev[0])) != RBC_OK) return s;
   for (size_t i = 0; i < g->items.size(); ++i) {
     const rbc_group_item& it = g->items[i];
     char* w = ws + g->ws_off[i];
-    rbc_status s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 0, it.A, it.lda, w, tab, st);
-    if (s == RBC_OK) s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 1, it.B, it.ldb, w, tab, st);
+    cudaStream_t si = g->side[i % ns];
+    s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 0, it.A, it.lda, w, tab, si);
+    if (s == RBC_OK) s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 1, it.B, it.ldb, w, tab, si);
     if (s != RBC_OK) return s;
   }
-  rbc_status s = grouped_gemm(g, ws, st);
-  if (s != RBC_OK) return s;
+  if ((s = join(g, st, &g->ev[2])) != RBC_OK) return s;
+  if ((s = grouped_gemm(g, ws, st)) != RBC_OK) return s;
+  if ((s = fork(g, st, g->ev[1])) != RBC_OK) return s;
   for (size_t i = 0; i < g->items.size(); ++i) {
     const rbc_group_item& it = g->items[i];
     if (it.plan->L == 0) continue;  // the leaf launch wrote C directly
-    s = decode_passes<float>(it.plan, g->layouts[i], it.C, it.ldc, ws + g->ws_off[i], tab, st);
+    s = decode_passes<float>(it.plan, g->layouts[i], it.C, it.ldc, ws + g->ws_off[i], tab, g->side[i % ns]);
     if (s != RBC_OK) return s;
   }
-  return RBC_OK;
+  return join(g, st, &g->ev[2 + ns]);
 }
 
 rbc_status check_ws(const rbc_group_s* g, void* ws, size_t bytes) {
