@@ -50,10 +50,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--decode", type=int, default=0, help="0 auto, 1 fused, 2 staged")
     ap.add_argument("--no-errors", action="store_true", help="skip the error pass after the timing")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
                     help="sweep: the at-scale fp32 sweep (default); batch: 512 uneven instances in one "
                          "grouped leaf launch replayed from a CUDA graph")
     ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--cap-gb", type=float, default=120.0, help="workspace admission cap of the queue")
     return ap.parse_args()
 
 
@@ -546,8 +549,143 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+SERVE_LEAF = {"fp32": "3xbf16", "bf16-leaf": "bf16", "3xbf16-leaf": "3xbf16"}
+
+
+def serve_specs(count: int, rate: float, seed: int = 5):
+    """Requests: exponential inter-arrival gaps (rate per second), n log-uniform in
+    [128, 8192], formula uniform over {strassen, laderman, noisy-strassen}, L uniform in
+    {1, 2, 3} but at most max(1, floor(log_n0(n / 64))) so that small n stay small, n rounded
+    up to a multiple of n0^L * 64, dtype uniform over {fp32, bf16-leaf, 3xbf16-leaf}."""
+    import math
+
+    import numpy as np
+    g = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += g.exponential(1.0 / rate)
+        name = ["strassen", "laderman", "noisy-strassen"][int(g.integers(0, 3))]
+        n0 = 3 if name == "laderman" else 2
+        n = math.exp(g.uniform(math.log(128), math.log(8192)))
+        L = int(g.integers(1, 4))
+        L = max(1, min(L, int(math.floor(math.log(max(n, 64) / 64.0) / math.log(n0) + 1e-9))))
+        q = n0**L * 64
+        n = int(math.ceil(n / q) * q)
+        dt = ["fp32", "bf16-leaf", "3xbf16-leaf"][int(g.integers(0, 3))]
+        out.append({"t": t, "formula": name, "n": n, "L": L, "dtype": dt, "seed": 50000 + i})
+    return out
+
+
+def run_serve(args):
+    import time as _t
+
+    import numpy as np
+    import torch
+
+    import paper_1905_07439_gb300 as rbc
+    from rbc_inputs import formula_by_name
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = serve_specs(args.requests, args.rate)
+    nmax = max(r["n"] for r in specs)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(17)
+    A = torch.randn((nmax, nmax), generator=gen, device=dev)   # request i uses the leading n x n block
+    B = torch.randn((nmax, nmax), generator=gen, device=dev)
+    forms = {nm: formula_by_name(nm, seed=7) for nm in ("strassen", "laderman", "noisy-strassen")}
+    plans = [rbc.Plan(*forms[r["formula"]], levels=r["L"], seed=r["seed"]) for r in specs]
+    slots = [torch.empty((nmax, nmax), device=dev) for _ in range(40)]
+    free = list(range(len(slots)))
+
+    def run_queue(paced: bool):
+        q = rbc.Queue(device=local, workspace_cap=int(args.cap_gb * (1 << 30)), streams=16)
+        live = {}  # ticket -> (index, slot)
+        done_t = [0.0] * len(specs)
+        t0 = _t.perf_counter()
+        i = 0
+
+        def collect():
+            for t in list(live):
+                if q.poll(t):
+                    idx, sl = live.pop(t)
+                    done_t[idx] = _t.perf_counter() - t0
+                    free.append(sl)
+
+        while i < len(specs) or live:
+            now = _t.perf_counter() - t0
+            while i < len(specs) and (not paced or specs[i]["t"] <= now) and free:
+                r = specs[i]
+                sl = free.pop()
+                n = r["n"]
+                Cv = slots[sl][:n, :n]
+                tk = q.submit(plans[i], A[:n, :n], B[:n, :n], Cv, rbc.LEAF_NAMES[SERVE_LEAF[r["dtype"]]])
+                live[tk] = (i, sl)
+                i += 1
+            collect()
+        stats = q.stats()
+        q.close()
+        return done_t, stats
+
+    run_queue(False)                       # warm-up (kernels loaded, pools touched)
+    done_t, stats = run_queue(True)        # Poisson arrivals
+    arrive = np.array([r["t"] for r in specs])
+    lat = (np.array(done_t) - arrive) * 1e3
+    span = max(done_t) - arrive[0]
+    closed_t, _ = run_queue(False)         # all requests available at once: capacity
+    cap_rps = len(specs) / max(closed_t)
+    # one at a time, fp32 leaves on the CUDA cores, on a sample of the requests
+    sample = list(range(0, len(specs), max(1, len(specs) // 300)))
+    ws = torch.empty(max(plans[i].workspace_size(specs[i]["n"], rbc.IO_F32, rbc.LEAF_F32) for i in sample),
+                     dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    t1 = _t.perf_counter()
+    for i in sample:
+        n = specs[i]["n"]
+        rbc.matmul(plans[i], A[:n, :n], B[:n, :n], slots[0][:n, :n], leaf=rbc.LEAF_F32, workspace=ws)
+        torch.cuda.synchronize(dev)
+    base_rps = len(sample) / (_t.perf_counter() - t1)
+    # one at a time with the served leaf modes (isolates the effect of concurrent admission)
+    t1 = _t.perf_counter()
+    for i in sample:
+        n = specs[i]["n"]
+        lf = rbc.LEAF_NAMES[SERVE_LEAF[specs[i]["dtype"]]]
+        wsz = plans[i].workspace_size(n, rbc.IO_F32, lf)
+        if wsz > ws.numel():
+            ws = torch.empty(wsz, dtype=torch.uint8, device=dev)
+        rbc.matmul(plans[i], A[:n, :n], B[:n, :n], slots[0][:n, :n], leaf=lf, workspace=ws)
+        torch.cuda.synchronize(dev)
+    same_rps = len(sample) / (_t.perf_counter() - t1)
+    eff = sum(2.0 * r["n"] ** 3 for r in specs)
+    line = {
+        "metric": METRIC, "value": round(len(specs) / span, 2), "unit": "requests/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": round(span * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 io; leaves per request (fp32 -> 3xbf16, bf16, 3xbf16)",
+        "data": "synthetic (seeded N(0,1); Poisson arrivals)",
+        "config": {"workload": f"rbc-serve: {len(specs)} requests, Poisson {args.rate:g}/s, n log-uniform "
+                               "[128,8192], strassen/laderman/noisy-strassen, L in {1,2,3} (clamped for small n), "
+                               "dtype in {fp32, bf16-leaf, 3xbf16-leaf}, workspace admission cap "
+                               f"{args.cap_gb:g} GB, 16 streams", "parallelism": "replicas x1"},
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),
+                       "max": round(float(lat.max()), 3)},
+        "effective_tflops": round(eff / span / 1e12, 2),
+        "capacity_requests_per_s": round(cap_rps, 1),
+        "one_at_a_time_fp32_requests_per_s": round(base_rps, 1),
+        "one_at_a_time_same_leaves_requests_per_s": round(same_rps, 1),
+        "capacity_vs_one_at_a_time_fp32": round(cap_rps / base_rps, 2),
+        "queue": {k: stats[k] for k in ("admitted", "completed", "workspace_peak", "peak_running")},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.workload == "serve" and args.impl != "reference":
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

@@ -237,6 +237,46 @@ rbc_status rbc_group_tune(rbc_group_t group, void* workspace, size_t workspace_b
                           rbc_group_tuning* out);
 void rbc_group_destroy(rbc_group_t group);
 
+/* Serving queue: independent products submitted as they arrive and served with continuous
+ * admission.  A worker thread admits requests in arrival order as soon as a stream and enough
+ * of the queue's device workspace pool are free (the pool is one region of `workspace_cap`
+ * bytes, allocated at creation); admitted requests run on their own streams, so work from
+ * requests that arrived while others were running overlaps on the device.  Each request is
+ * computed exactly as rbc_matmul computes it.  Submit and poll may be called from any host
+ * thread; poll never blocks. */
+typedef struct rbc_queue_s* rbc_queue_t;
+
+typedef struct {
+  rbc_plan_t plan;
+  const void* A;   /* device; A, B, C stay valid and untouched until the request is collected */
+  const void* B;
+  void* C;
+  int64_t N, lda, ldb, ldc;
+  int io_dtype, leaf_dtype;
+} rbc_request;
+
+typedef struct {
+  int64_t pending, running;
+  uint64_t admitted, completed;
+  size_t workspace_used, workspace_peak, workspace_cap;
+  int peak_running;
+} rbc_queue_info;
+
+/* Create a queue on `device` with a workspace pool of workspace_cap bytes (one cudaMalloc)
+ * and `streams` streams (1..256).  RBC_ENOMEM if the pool cannot be allocated. */
+rbc_status rbc_queue_create(int device, size_t workspace_cap, int streams, rbc_queue_t* out);
+/* Enqueue `count` requests; they receive tickets *ticket, *ticket + 1, ...  A request whose
+ * arguments are invalid completes at once with RBC_EINVAL; one whose workspace exceeds the
+ * whole pool is refused (RBC_ENOMEM, nothing enqueued). */
+rbc_status rbc_batch_submit(rbc_queue_t queue, const rbc_request* reqs, int count, uint64_t* ticket);
+/* Non-blocking completion check: *done = 0 (waiting or running) or 1 (finished; the ticket is
+ * then collected and forgotten).  Returns the request's own status when it finished with an
+ * error (e.g. RBC_ETIMEOUT from a bounded device wait), RBC_EINVAL for an unknown ticket. */
+rbc_status rbc_batch_poll(rbc_queue_t queue, uint64_t ticket, int* done);
+rbc_status rbc_queue_stats(rbc_queue_t queue, rbc_queue_info* info);
+/* Finish every submitted request, then release the streams and the pool. */
+void rbc_queue_destroy(rbc_queue_t queue);
+
 /* Device-side status of the calls that used `workspace` (its first 4 bytes, cleared by every
  * rbc_matmul): waits for `stream`, copies the word to *device_status and clears it.  0 means
  * no error; RBC_ETIMEOUT means a bounded wait inside a kernel expired and that kernel skipped

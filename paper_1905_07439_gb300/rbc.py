@@ -48,6 +48,18 @@ class rbc_group_tuning(C.Structure):
 RBC_GROUP_GRAPH = 1
 
 
+class rbc_request(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("A", C.c_void_p), ("B", C.c_void_p), ("C", C.c_void_p),
+                ("N", C.c_int64), ("lda", C.c_int64), ("ldb", C.c_int64), ("ldc", C.c_int64),
+                ("io_dtype", C.c_int), ("leaf_dtype", C.c_int)]
+
+
+class rbc_queue_info(C.Structure):
+    _fields_ = [("pending", C.c_int64), ("running", C.c_int64), ("admitted", C.c_uint64),
+                ("completed", C.c_uint64), ("workspace_used", C.c_size_t), ("workspace_peak", C.c_size_t),
+                ("workspace_cap", C.c_size_t), ("peak_running", C.c_int)]
+
+
 class rbc_matmul_opts(C.Structure):
     _fields_ = [("decode", C.c_int), ("reserved", C.c_int * 7), ("events", C.c_void_p * 4),
                 ("launches", C.c_int64)]
@@ -74,6 +86,11 @@ SIGNATURES = {
     "rbc_group_run": (C.c_int, [_P, _P, C.c_size_t, _P, C.c_int]),
     "rbc_group_tune": (C.c_int, [_P, _P, C.c_size_t, _P, C.POINTER(rbc_group_tuning)]),
     "rbc_group_destroy": (None, [_P]),
+    "rbc_queue_create": (C.c_int, [C.c_int, C.c_size_t, C.c_int, C.POINTER(_P)]),
+    "rbc_batch_submit": (C.c_int, [_P, C.POINTER(rbc_request), C.c_int, C.POINTER(C.c_uint64)]),
+    "rbc_batch_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int)]),
+    "rbc_queue_stats": (C.c_int, [_P, C.POINTER(rbc_queue_info)]),
+    "rbc_queue_destroy": (None, [_P]),
     "rbc_matmul_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int,
                                     C.c_int, _P]),
     "rbc_static_scratch_bytes": (C.c_size_t, []),
@@ -276,3 +293,45 @@ class Group:
         check(lib().rbc_group_tune(self.handle, workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
                                    C.byref(t)), "rbc_group_tune")
         return {"bn": t.bn, "group": t.group, "candidates": t.candidates, "best_ms": t.best_ms}
+
+
+class Queue:
+    """Owner of an rbc_queue_t (continuous-admission serving queue)."""
+
+    def __init__(self, device: int = 0, workspace_cap: int = 1 << 30, streams: int = 16):
+        h = _P()
+        check(lib().rbc_queue_create(device, workspace_cap, streams, C.byref(h)), "rbc_queue_create")
+        self.handle = h
+        self._live = {}   # ticket -> tensors kept alive until collected
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib().rbc_queue_destroy(h)
+            self.handle = None
+            self._live.clear()
+
+    __del__ = close
+
+    def submit(self, plan: "Plan", A, B, C_out, leaf: int) -> int:
+        io = _io_of(A)
+        r = rbc_request(plan.handle.value, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), A.shape[0],
+                        A.stride(0), B.stride(0), C_out.stride(0), io, leaf)
+        t = C.c_uint64()
+        check(lib().rbc_batch_submit(self.handle, C.byref(r), 1, C.byref(t)), "rbc_batch_submit")
+        self._live[t.value] = (plan, A, B, C_out)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        """True once the request has finished (raises RbcError if it failed)."""
+        d = C.c_int()
+        st = lib().rbc_batch_poll(self.handle, ticket, C.byref(d))
+        if d.value:
+            self._live.pop(ticket, None)
+        check(st, "rbc_batch_poll")
+        return bool(d.value)
+
+    def stats(self) -> dict:
+        i = rbc_queue_info()
+        check(lib().rbc_queue_stats(self.handle, C.byref(i)), "rbc_queue_stats")
+        return {f: getattr(i, f) for f, _ in rbc_queue_info._fields_}
