@@ -175,6 +175,38 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
                          void* workspace, size_t workspace_bytes, void* stream,
                          rbc_matmul_opts* opts);
 
+/* Independent realizations F^(L)_1 .. F^(L)_K of the same product (Section 3: the error of
+ * an average of realizations, Eq. error-of-average, and the spread of single realizations,
+ * Eq. average-of-error).  Realization k uses plans[k] (its draws); every plan must describe
+ * the same computation otherwise (U, V, W, R, n0, levels, rand_mode, draw_scope, rescaling:
+ * RBC_EINVAL if not).  A, B: device, N x N, shared by all realizations.  Output k:
+ * C + k * strideC (elements; strideC >= ldc * N when count > 1), N x N with leading dim ldc.
+ * The draws of as many realizations as the workspace holds are processed by each launch
+ * (staged decode); rbc_realizations_workspace_size(plan, N, io, leaf, count) is the
+ * workspace that holds all of them at once, and any workspace of at least the size for
+ * count = 1 works (the realizations then run in consecutive batches on the stream).
+ * Leaf modes and dtypes as rbc_matmul.  L = 0 computes the same standard product K times. */
+size_t rbc_realizations_workspace_size(rbc_plan_t plan, int64_t N, int io_dtype, int leaf_dtype,
+                                       int64_t count);
+rbc_status rbc_matmul_realizations(const rbc_plan_t* plans, int64_t count, const void* A,
+                                   const void* B, void* C, int64_t N, int64_t lda, int64_t ldb,
+                                   int64_t ldc, int64_t strideC, int io_dtype, int leaf_dtype,
+                                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* Relative Frobenius errors of K realizations against a reference product (Section 3),
+ * in fp64 with a fixed summation order (bit-identical on repeated calls):
+ *   RBC_ERR_EACH:    err[k]     = ||C_k - Ref||_F / ||Ref||_F              (Eq. average-of-error)
+ *   RBC_ERR_AVERAGE: err[n - 1] = ||(1/n) sum_{k<n} C_k - Ref||_F / ||Ref||_F, n = 1..K
+ *                                                                          (Eq. error-of-average)
+ * C: device, K matrices N x N of dtype c_dtype (rbc_io_dtype) at C + k * strideC, leading dim
+ * ldc.  Ref: device fp64, N x N, leading dim ldr.  err: device, K doubles.  work: device
+ * scratch of rbc_realization_errors_work_size(K, N) bytes.  ||Ref|| = 0 gives inf/nan. */
+typedef enum { RBC_ERR_EACH = 0, RBC_ERR_AVERAGE = 1 } rbc_err_mode;
+rbc_status rbc_realization_errors(const void* C, int c_dtype, int64_t K, int64_t N, int64_t ldc,
+                                  int64_t strideC, const double* Ref, int64_t ldr, int mode,
+                                  double* err, void* work, size_t work_bytes, void* stream);
+size_t rbc_realization_errors_work_size(int64_t K, int64_t N);
+
 /* rbc_matmul without a caller workspace, for callers that cannot allocate device memory
  * when they multiply (a framework that has reserved the whole device heap for its own
  * allocator, code allowed to allocate only at start-up, paths that cannot handle an

@@ -88,11 +88,17 @@ __host__ __device__ inline int subtree_nodes(int R, int G) {
 // Local id of the node at relative depth j with path prefix q: sum_{i<j} R^i + q.
 __device__ __forceinline__ int local_id(int R, int j, int q) { return subtree_nodes(R, j) + q; }
 
-// Expand the tables of the G-level subtree under parent heap id hp (at depth a.depth) into
+// Expand the tables of the G-level subtree under launch parent p (at depth a.depth) into
 // coef[(local * R + r) * n0^2 + a * n0 + b] for tensor `which` (0 u^, 1 v^, 2 w^).
 template <typename Tc>
-__device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, int which, int64_t hp,
+__device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, int which, int64_t p,
                                Tc* coef) {
+  int64_t real = 0, hp = a.node_first + p;
+  if (a.real_parents > 0) {
+    real = p / a.real_parents;
+    hp = a.node_first + (p - real * a.real_parents);
+  }
+  const uint64_t* draws = t.draw + real * a.real_draws;
   const int R = t.R, n0 = t.n0, nn = n0 * n0;
   const int total = subtree_nodes(R, G) * R * nn;
   const Tc* base = which == 0 ? t.U : (which == 1 ? t.V : t.W);
@@ -113,7 +119,7 @@ __device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, in
     int64_t rj = 1;
     for (int i = 0; i < j; ++i) rj *= R;
     const int64_t heap = hp * rj + (int64_t)local;  // descendant of hp: hp*R^j + sum_{i<j} R^i + q
-    const uint64_t w = t.per_level ? t.draw[a.depth + j] : t.draw[a.dbase[j] + (heap - a.dfirst[j])];
+    const uint64_t w = t.per_level ? draws[a.depth + j] : draws[a.dbase[j] + (heap - a.dfirst[j])];
     const Tc v = base[(draw_perm(w, cr, ra) * n0 + draw_perm(w, cc, cb)) * R + r];
     coef[e] = sc * v * (Tc)draw_sign(w, cr, ra) * (Tc)draw_sign(w, cc, cb);
   }
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
   const int64_t outs = a.outs_per_parent;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();  // the previous parent's readers are done with the tables
-    expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
+    expand_subtree(t, a, G, a.tensor, p, coef);
     __syncthreads();
     if (!inside) continue;
     EncodeEmitV<Tc, S, VEC> emit;
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(256) encode_pass_trans_kernel(const __grid_con
   const bool valid = y < a.nb && x < a.nb;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();
-    expand_subtree(t, a, G, a.tensor, a.node_first + p, coef);
+    expand_subtree(t, a, G, a.tensor, p, coef);
     __syncthreads();
     TransposedEmit<Tc, S> emit;
     emit.tile = tile;
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
   const bool valid = x < a.nb && y < a.nb;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();
-    expand_subtree(t, a, G, 2, a.node_first + p, coef);
+    expand_subtree(t, a, G, 2, p, coef);
     __syncthreads();
     if (!valid) continue;
     DecodeFetch<Tm, Tc, VEC> fetch;

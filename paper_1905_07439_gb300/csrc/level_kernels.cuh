@@ -16,6 +16,9 @@ namespace rbc {
 //           leading dim ldx, nb x nb valid); Y = parents (p*strideY, leading dim ldy).
 // Draw set of a node at relative depth j with heap id n: draw[dbase[j] + n - dfirst[j]]
 // (per-node scope) or draw[depth + j] (per-level scope).
+// Realization batches: with real_parents > 0 the parents of the launch belong to consecutive
+// independent realizations, real_parents each; parent p is node node_first + p % real_parents
+// of realization p / real_parents, whose draw sets start at draw[(p / real_parents) * real_draws].
 struct PassArgs {
   const void* X;
   int64_t ldx, strideX;
@@ -26,6 +29,8 @@ struct PassArgs {
   int64_t parents;
   int64_t outs_per_parent;
   int64_t node_first;
+  int64_t real_parents;  // 0: all parents belong to one realization
+  int64_t real_draws;
   int depth;
   int tensor;     // encode: 0 left operand (u^), 1 right operand (v^)
   int split;      // encode: write [hi | lo] panels

@@ -63,8 +63,12 @@ double fused_contributions(const rbc_plan_s* p) {
   return c;
 }
 
-rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo) {
+rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo,
+                       int64_t reals) {
   if (!p) return fail(RBC_EINVAL, "null plan");
+  if (reals < 1) return fail(RBC_EINVAL, "realization count must be positive");
+  if (reals > 1 && (p->L == 0 || decode_req != 2))
+    return fail(RBC_EINVAL, "realization batches need L >= 1 and staged decode");
   if (io != RBC_IO_F32 && io != RBC_IO_F64) return fail(RBC_EINVAL, "bad io dtype");
   if (leaf < RBC_LEAF_F64 || leaf > RBC_LEAF_3XTF32) return fail(RBC_EINVAL, "bad leaf dtype");
   if (io == RBC_IO_F64 && leaf != RBC_LEAF_F64)
@@ -104,13 +108,13 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   for (int i = 1; i < lo->passes.count; ++i) {
     const int d = lo->passes.top[i];
     const int64_t nd = lo->m * ipow(n0, L - d);
-    const size_t bytes = align256((size_t)ipow(R, d) * nd * pad_ld(nd) * lo->es_io);
+    const size_t bytes = align256((size_t)(reals * ipow(R, d)) * nd * pad_ld(nd) * lo->es_io);
     lo->encA[d] = off;
     off += bytes;
     lo->encB[d] = off;
     off += bytes;
   }
-  const int64_t leaves = ipow(R, L);
+  const int64_t leaves = reals * ipow(R, L);
   const size_t leaf_bytes = align256((size_t)leaves * lo->mp * lo->K * lo->es_leaf);
   lo->leafS = off;
   off += leaf_bytes;
@@ -123,7 +127,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
       const int d = lo->passes.top[i];
       const int64_t nd = lo->m * ipow(n0, L - d);
       lo->dec[d] = off;
-      off += align256((size_t)ipow(R, d) * nd * pad_ld(nd) * lo->es_acc);
+      off += align256((size_t)(reals * ipow(R, d)) * nd * pad_ld(nd) * lo->es_acc);
     }
   }
   lo->total = off;
@@ -135,24 +139,6 @@ struct TablesBox {
   std::unique_ptr<Tables<T>> t{new Tables<T>()};
 };
 
-// Load the draw sets of parents [c0, c0 + cnt) at depth d and their subtrees over g levels.
-template <typename T>
-rbc_status pass_tables(const rbc_plan_s* p, int d, int g, int64_t c0, int64_t cnt, PassArgs* a, Tables<T>& tab) {
-  a->depth = d;
-  a->node_first = depth_start(p->R, d) + c0;
-  if (p->scope == RBC_DRAW_PER_LEVEL) return fill_tables(p, 0, p->draw_count, &tab);
-  int64_t first[kMaxLevels], count[kMaxLevels], base = 0;
-  for (int j = 0; j < g; ++j) {
-    const int64_t rj = ipow(p->R, j);
-    first[j] = depth_start(p->R, d + j) + c0 * rj;
-    count[j] = cnt * rj;
-    a->dfirst[j] = first[j];
-    a->dbase[j] = base;
-    base += count[j];
-  }
-  return fill_tables_ranges(p, first, count, g, &tab);
-}
-
 // Parents per launch so that the subtree draws of a chunk fit the kernel table.
 int64_t pass_chunk(const rbc_plan_s* p, int g, int64_t parents) {
   if (p->scope == RBC_DRAW_PER_LEVEL) return parents;
@@ -162,11 +148,86 @@ int64_t pass_chunk(const rbc_plan_s* p, int g, int64_t parents) {
   return c < 1 ? 1 : c;
 }
 
+// Draw sets one realization needs for parents [c0, c0 + cnt) at depth d and their subtrees
+// over g levels (per-node scope), or all of its levels (per-level scope).
+int64_t launch_draws(const rbc_plan_s* p, int g, int64_t cnt) {
+  if (p->scope == RBC_DRAW_PER_LEVEL) return p->draw_count;
+  int64_t n = 0;
+  for (int j = 0; j < g; ++j) n += cnt * ipow(p->R, j);
+  return n;
+}
+
+// Every launch of the pass at depth d over g levels: f(k0, kc, c0, cnt) covers realizations
+// [k0, k0 + kc) and, in each, parents [c0, c0 + cnt).  When the draw sets of a whole
+// realization fit the kernel table, as many realizations as fit share a launch; otherwise
+// one realization at a time, its parents chunked.
+template <class F>
+rbc_status for_each_launch(const Reals& rs, int d, int g, F&& f) {
+  const rbc_plan_s* p = rs.plans[0];
+  const int64_t P = ipow(p->R, d);
+  const int64_t D = launch_draws(p, g, P);
+  if (D <= kMaxDraws) {
+    const int64_t rc = D > 0 ? std::max<int64_t>(1, kMaxDraws / D) : rs.count;
+    for (int64_t k0 = 0; k0 < rs.count; k0 += rc) {
+      const rbc_status s = f(k0, std::min(rc, rs.count - k0), (int64_t)0, P);
+      if (s != RBC_OK) return s;
+    }
+    return RBC_OK;
+  }
+  const int64_t chunk = pass_chunk(p, g, P);
+  for (int64_t k = 0; k < rs.count; ++k)
+    for (int64_t c0 = 0; c0 < P; c0 += chunk) {
+      const rbc_status s = f(k, (int64_t)1, c0, std::min(chunk, P - c0));
+      if (s != RBC_OK) return s;
+    }
+  return RBC_OK;
+}
+
+// Tables of one launch: base tensors of the formula and, realization after realization, the
+// draw sets of parents [c0, c0 + cnt) at depth d with their g-level subtrees.
+template <typename T>
+rbc_status launch_tables(const Reals& rs, int d, int g, int64_t k0, int64_t kc, int64_t c0, int64_t cnt, PassArgs* a,
+                         Tables<T>& tab) {
+  const rbc_plan_s* p = rs.plans[k0];
+  rbc_status s = fill_tables(p, 0, 0, &tab);
+  if (s != RBC_OK) return s;
+  a->depth = d;
+  a->node_first = depth_start(p->R, d) + c0;
+  a->real_parents = cnt;
+  int64_t first[kMaxLevels], count[kMaxLevels], nr = 0, per = 0;
+  if (p->scope == RBC_DRAW_PER_LEVEL) {
+    first[0] = 0;
+    count[0] = p->draw_count;
+    nr = 1;
+    per = p->draw_count;
+  } else {
+    for (int j = 0; j < g; ++j) {
+      const int64_t rj = ipow(p->R, j);
+      first[j] = depth_start(p->R, d + j) + c0 * rj;
+      count[j] = cnt * rj;
+      a->dfirst[j] = first[j];
+      a->dbase[j] = per;
+      per += count[j];
+    }
+    nr = g;
+  }
+  if (kc * per > kMaxDraws) return fail(RBC_EUNSUPPORTED, "one launch needs more than 1024 draw sets");
+  a->real_draws = per;
+  int64_t o = 0;
+  for (int64_t k = 0; k < kc; ++k) {
+    const rbc_plan_s* q = rs.plans[k0 + k];
+    for (int i = 0; i < nr; ++i)
+      for (int64_t e = 0; e < count[i]; ++e) tab.draw[o++] = q->packed[first[i] + e];
+  }
+  return RBC_OK;
+}
+
 // Encode one operand through all passes into the leaf operand buffer (row-major, K-major
 // rows of length lo.K, zero padded to mp, split panels [hi | lo]).
 template <typename T>
-rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
-                          int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st) {
+rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor, const void* X, int64_t ldx,
+                          char* ws, Tables<T>& tab, cudaStream_t st) {
+  const rbc_plan_s* p = rs.plans[0];
   const int L = p->L, R = p->R, n0 = p->n0;
   const size_t* enc = tensor == 0 ? lo.encA : lo.encB;
   char* leafbuf = ws + (tensor == 0 ? lo.leafS : lo.leafT);
@@ -192,24 +253,23 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
     const int d = lo.passes.top[i], g = lo.passes.g[i];
     const bool last = i + 1 == lo.passes.count;
     const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
-    const int64_t parents = ipow(R, d), outs = ipow(R, g);
-    const int64_t chunk = pass_chunk(p, g, parents);
-    for (int64_t c0 = 0; c0 < parents; c0 += chunk) {
-      const int64_t cnt = std::min(chunk, parents - c0);
+    const int64_t P = ipow(R, d), outs = ipow(R, g);
+    rbc_status s = for_each_launch(rs, d, g, [&](int64_t k0, int64_t kc, int64_t c0, int64_t cnt) {
       PassArgs a{};
-      rbc_status s = pass_tables(p, d, g, c0, cnt, &a, tab);
-      if (s != RBC_OK) return s;
+      rbc_status s2 = launch_tables(rs, d, g, k0, kc, c0, cnt, &a, tab);
+      if (s2 != RBC_OK) return s2;
+      const int64_t first = k0 * P + c0;  // first parent of the launch, realization-major
       if (d == 0) {
         a.X = X;
         a.ldx = ldx;
         a.strideX = 0;
       } else {
-        a.X = ws + enc[d] + (size_t)c0 * n_par * pad_ld(n_par) * lo.es_io;
+        a.X = ws + enc[d] + (size_t)first * n_par * pad_ld(n_par) * lo.es_io;
         a.ldx = pad_ld(n_par);
         a.strideX = n_par * pad_ld(n_par);
       }
       if (last) {
-        a.Y = leafbuf + (size_t)c0 * outs * lo.mp * lo.K * lo.es_leaf;
+        a.Y = leafbuf + (size_t)first * outs * lo.mp * lo.K * lo.es_leaf;
         a.ldy = lo.K;
         a.strideY = lo.mp * lo.K;
         a.rows_out = lo.mp;
@@ -219,66 +279,68 @@ rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int ten
         // tf32 tensor-core leaves take T K-major: write T^T
         a.trans = tensor == 1 && lo.store == kStoreTF32;
       } else {
-        a.Y = ws + enc[d + g] + (size_t)c0 * outs * nb * pad_ld(nb) * lo.es_io;
+        a.Y = ws + enc[d + g] + (size_t)first * outs * nb * pad_ld(nb) * lo.es_io;
         a.ldy = pad_ld(nb);
         a.strideY = nb * pad_ld(nb);
         a.rows_out = nb;
         a.cols_out = nb;
       }
       a.nb = nb;
-      a.parents = cnt;
+      a.parents = kc * cnt;
       a.outs_per_parent = outs;
       a.tensor = tensor;
       const int store = last ? lo.store : (io == RBC_IO_F64 ? kStoreF64 : kStoreF32);
       cudaError_t e = launch_encode_pass(tab, a, n0, g, io, store, st);
       ++g_launches;
-      if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
-    }
+      return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+    });
+    if (s != RBC_OK) return s;
   }
   return RBC_OK;
 }
 
-// Staged decode: passes from the leaves up to C.
+// Staged decode: passes from the leaves up to C (realization k's output at C + k * strideC).
 template <typename T>
-rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
-                         Tables<T>& tab, cudaStream_t st) {
+rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc, char* ws, Tables<T>& tab,
+                         cudaStream_t st) {
+  const rbc_plan_s* p = rs.plans[0];
   const int L = p->L, R = p->R, n0 = p->n0;
   for (int i = lo.passes.count - 1; i >= 0; --i) {
     const int d = lo.passes.top[i], g = lo.passes.g[i];
     const bool bottom = i + 1 == lo.passes.count;
     const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
-    const int64_t parents = ipow(R, d), outs = ipow(R, g);
-    const int64_t chunk = pass_chunk(p, g, parents);
-    for (int64_t c0 = 0; c0 < parents; c0 += chunk) {
-      const int64_t cnt = std::min(chunk, parents - c0);
+    const int64_t P = ipow(R, d), outs = ipow(R, g);
+    rbc_status s = for_each_launch(rs, d, g, [&](int64_t k0, int64_t kc, int64_t c0, int64_t cnt) {
       PassArgs a{};
-      rbc_status s = pass_tables(p, d, g, c0, cnt, &a, tab);
-      if (s != RBC_OK) return s;
+      rbc_status s2 = launch_tables(rs, d, g, k0, kc, c0, cnt, &a, tab);
+      if (s2 != RBC_OK) return s2;
+      const int64_t first = k0 * P + c0;
       if (bottom) {
-        a.X = ws + lo.M + (size_t)c0 * outs * lo.mp * lo.mp * lo.es_acc;
+        a.X = ws + lo.M + (size_t)first * outs * lo.mp * lo.mp * lo.es_acc;
         a.ldx = lo.mp;
         a.strideX = lo.mp * lo.mp;
       } else {
-        a.X = ws + lo.dec[d + g] + (size_t)c0 * outs * nb * pad_ld(nb) * lo.es_acc;
+        a.X = ws + lo.dec[d + g] + (size_t)first * outs * nb * pad_ld(nb) * lo.es_acc;
         a.ldx = pad_ld(nb);
         a.strideX = nb * pad_ld(nb);
       }
-      if (d == 0) {
-        a.Y = C;
+      if (d == 0) {  // one parent per realization
+        a.Y = static_cast<char*>(C) + (size_t)k0 * rs.strideC * lo.es_io;
         a.ldy = ldc;
-        a.strideY = 0;
+        a.strideY = rs.strideC;
       } else {
-        a.Y = ws + lo.dec[d] + (size_t)c0 * n_par * pad_ld(n_par) * lo.es_acc;
+        a.Y = ws + lo.dec[d] + (size_t)first * n_par * pad_ld(n_par) * lo.es_acc;
         a.ldy = pad_ld(n_par);
         a.strideY = n_par * pad_ld(n_par);
       }
       a.nb = nb;
-      a.parents = cnt;
+      a.parents = kc * cnt;
       a.outs_per_parent = outs;
       cudaError_t e = launch_decode_pass(tab, a, n0, g, st);
       ++g_launches;
-      if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
-    }
+      return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+    });
+    if (s != RBC_OK) return s;
   }
   return RBC_OK;
 }
@@ -288,18 +350,19 @@ inline void mark(const rbc_matmul_opts* o, int i, cudaStream_t st) {
 }
 
 template <typename T>
-rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void* B, void* C, int64_t N,
+rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, void* C, int64_t N,
                int64_t lda, int64_t ldb, int64_t ldc, int io, int leaf, char* ws, cudaStream_t st,
                const rbc_matmul_opts* opts) {
   static thread_local TablesBox<T> box;
   Tables<T>& tab = *box.t;
+  const rbc_plan_s* p = rs.plans[0];
   mark(opts, 0, st);
-  rbc_status s = encode_operand<T>(p, lo, io, 0, A, lda, ws, tab, st);
+  rbc_status s = encode_operand<T>(rs, lo, io, 0, A, lda, ws, tab, st);
   if (s != RBC_OK) return s;
-  s = encode_operand<T>(p, lo, io, 1, B, ldb, ws, tab, st);
+  s = encode_operand<T>(rs, lo, io, 1, B, ldb, ws, tab, st);
   if (s != RBC_OK) return s;
   const int L = p->L;
-  const int64_t leaves = ipow(p->R, L);
+  const int64_t leaves = rs.count * ipow(p->R, L);
   const bool fused = lo.decode == 1 || L == 0;
   if (fused && L > 0) {
     cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * lo.es_io, 0, (size_t)N * lo.es_io, (size_t)N, st);
@@ -307,8 +370,7 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
   }
   mark(opts, 1, st);
   if (fused) {
-    s = p->scope == RBC_DRAW_PER_LEVEL ? fill_tables(p, 0, p->draw_count, &tab)
-                                       : fill_tables(p, 0, p->draw_count, &tab);
+    s = fill_tables(p, 0, p->draw_count, &tab);
   } else {
     s = fill_tables(p, 0, 0, &tab);
   }
@@ -363,16 +425,16 @@ rbc_status run(const rbc_plan_s* p, const Layout& lo, const void* A, const void*
   }
   mark(opts, 2, st);
   if (!fused) {
-    s = decode_passes<T>(p, lo, C, ldc, ws, tab, st);
+    s = decode_passes<T>(rs, lo, C, ldc, ws, tab, st);
     if (s != RBC_OK) return s;
   }
   mark(opts, 3, st);
   return RBC_OK;
 }
 
-template rbc_status encode_operand<float>(const rbc_plan_s*, const Layout&, int, int, const void*, int64_t, char*,
+template rbc_status encode_operand<float>(const Reals&, const Layout&, int, int, const void*, int64_t, char*,
                                           Tables<float>&, cudaStream_t);
-template rbc_status decode_passes<float>(const rbc_plan_s*, const Layout&, void*, int64_t, char*, Tables<float>&,
+template rbc_status decode_passes<float>(const Reals&, const Layout&, void*, int64_t, char*, Tables<float>&,
                                          cudaStream_t);
 
 }  // namespace detail
@@ -412,12 +474,82 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);  // clear the status word
     if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
   }
+  const Reals rs{&plan, 1, 0};
   if (io == RBC_IO_F64)
-    s = run<double>(plan, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
+    s = run<double>(rs, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
   else
-    s = run<float>(plan, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
+    s = run<float>(rs, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
   if (opts) opts->launches = g_launches;
   return s;
+}
+
+// The plans of a realization batch must describe the same computation up to their draws.
+static rbc_status same_computation(const rbc_plan_s* a, const rbc_plan_s* b) {
+  if (!b) return fail(RBC_EINVAL, "null plan in the realization list");
+  if (a->R != b->R || a->n0 != b->n0 || a->L != b->L || a->mode != b->mode || a->scope != b->scope ||
+      a->scale != b->scale || a->U != b->U || a->V != b->V || a->W != b->W)
+    return fail(RBC_EINVAL, "realization plans differ in formula, depth, mode, scope or rescaling");
+  return RBC_OK;
+}
+
+size_t rbc_realizations_workspace_size(rbc_plan_t plan, int64_t N, int io, int leaf, int64_t count) {
+  if (!plan || count < 1) return 0;
+  Layout lo;
+  if (plan->L == 0) return make_layout(plan, N, io, leaf, 0, &lo) == RBC_OK ? lo.total : 0;
+  if (make_layout(plan, N, io, leaf, 2, &lo, count) != RBC_OK) return 0;
+  return lo.total;
+}
+
+rbc_status rbc_matmul_realizations(const rbc_plan_t* plans, int64_t count, const void* A, const void* B, void* C,
+                                   int64_t N, int64_t lda, int64_t ldb, int64_t ldc, int64_t strideC, int io,
+                                   int leaf, void* workspace, size_t ws_bytes, void* stream) {
+  if (!plans || count < 1 || !A || !B || !C) return fail(RBC_EINVAL, "null argument or empty realization list");
+  const rbc_plan_s* p0 = plans[0];
+  if (!p0) return fail(RBC_EINVAL, "null plan in the realization list");
+  for (int64_t k = 1; k < count; ++k) {
+    rbc_status s = same_computation(p0, plans[k]);
+    if (s != RBC_OK) return s;
+  }
+  if (lda < N || ldb < N || ldc < N) return fail(RBC_EINVAL, "leading dimension smaller than N");
+  if (count > 1 && strideC < ldc * N) return fail(RBC_EINVAL, "strideC smaller than ldc * N: outputs overlap");
+  if (!workspace || ((uintptr_t)workspace & 255))
+    return fail(RBC_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t es = io == RBC_IO_F64 ? 8 : 4;
+  if (p0->L == 0) {  // the classical product: every realization is the same computation
+    for (int64_t k = 0; k < count; ++k) {
+      rbc_status s = rbc_matmul_ex(plans[k], A, B, static_cast<char*>(C) + (size_t)k * strideC * es, N, lda, ldb,
+                                   ldc, io, leaf, workspace, ws_bytes, stream, nullptr);
+      if (s != RBC_OK) return s;
+    }
+    return RBC_OK;
+  }
+  Layout one;
+  rbc_status s = make_layout(p0, N, io, leaf, 2, &one, 1);
+  if (s != RBC_OK) return s;
+  if (ws_bytes < one.total) return fail(RBC_ENOMEM, "workspace smaller than one realization needs");
+  // The largest batch whose layout fits: a batch of b needs at most kStatusBytes + b * (one
+  // realization's bytes beyond the status words).
+  const size_t per = one.total - kStatusBytes;
+  int64_t batch = (int64_t)std::min<size_t>((size_t)count, (ws_bytes - kStatusBytes) / per);
+  Layout lo;
+  s = make_layout(p0, N, io, leaf, 2, &lo, batch);
+  if (s != RBC_OK) return s;
+  char* ws = static_cast<char*>(workspace);
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);
+  if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
+  for (int64_t k0 = 0; k0 < count; k0 += batch) {
+    const int64_t kc = std::min(batch, count - k0);
+    Layout lk;
+    s = kc == batch ? RBC_OK : make_layout(p0, N, io, leaf, 2, &lk, kc);
+    if (s != RBC_OK) return s;
+    const Reals rs{plans + k0, kc, strideC};
+    void* Ck = static_cast<char*>(C) + (size_t)k0 * strideC * es;
+    s = io == RBC_IO_F64 ? run<double>(rs, kc == batch ? lo : lk, A, B, Ck, N, lda, ldb, ldc, io, leaf, ws, st, nullptr)
+                         : run<float>(rs, kc == batch ? lo : lk, A, B, Ck, N, lda, ldb, ldc, io, leaf, ws, st, nullptr);
+    if (s != RBC_OK) return s;
+  }
+  return RBC_OK;
 }
 
 rbc_status rbc_workspace_check(void* workspace, void* stream, int* device_status) {

@@ -38,16 +38,39 @@ struct Layout {
   size_t total = 0;
 };
 
+// Independent realizations computed together: plans[k], k < count, which share the formula,
+// depth, randomization mode, draw scope and rescaling and differ in their draws.  Their
+// intermediates sit realization-major in one workspace; output k is C + k * strideC.
+struct Reals {
+  const rbc_plan_s* const* plans = nullptr;
+  int64_t count = 1;
+  int64_t strideC = 0;  // elements
+};
+
 bool is_tc_leaf(int leaf);
 Passes plan_passes(int L, int n0);
-rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo);
+// reals > 1: the layout of that many realizations (staged decode only).
+rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo,
+                       int64_t reals = 1);
 
 template <typename T>
-rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
-                          int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st);
+rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor, const void* X, int64_t ldx,
+                          char* ws, Tables<T>& tab, cudaStream_t st);
 template <typename T>
-rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
-                         Tables<T>& tab, cudaStream_t st);
+rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc, char* ws, Tables<T>& tab,
+                         cudaStream_t st);
+template <typename T>
+inline rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
+                                 int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st) {
+  const Reals rs{&p, 1, 0};
+  return encode_operand<T>(rs, lo, io, tensor, X, ldx, ws, tab, st);
+}
+template <typename T>
+inline rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
+                                Tables<T>& tab, cudaStream_t st) {
+  const Reals rs{&p, 1, 0};
+  return decode_passes<T>(rs, lo, C, ldc, ws, tab, st);
+}
 
 }  // namespace detail
 }  // namespace rbc

@@ -77,10 +77,155 @@ cudaError_t launch_norms(const void* X, const void* Y, int64_t rows, int64_t col
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- realization errors
+// Errors of K realizations against a reference (Section 3).  Each CTA owns kErrPer elements
+// (kErrEpt per thread, strided by the block size so that loads coalesce) and writes one
+// partial sum of squared differences per realization (EACH) or per prefix length (AVERAGE:
+// running sums of the realizations in fp64, the average formed as sum / n).  A final CTA
+// sums the partials of every realization in CTA order.
+constexpr int kErrThreads = 256, kErrEpt = 4, kErrPer = kErrThreads * kErrEpt;
+
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kErrThreads / 32; ++w) s += sm[w];
+  return s;  // valid in thread 0
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kErrThreads)
+    err_each_kernel(const TC* C, int64_t K, int64_t N, int64_t ldc, int64_t strideC, const double* Ref,
+                    int64_t ldr, double* part, int64_t nblk) {
+  __shared__ double sm[2][kErrThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kErrPer + threadIdx.x, total = N * N;
+  int it = 0;
+  for (int64_t k = blockIdx.y; k < K; k += gridDim.y, ++it) {
+    double d2 = 0.0;
+#pragma unroll
+    for (int v = 0; v < kErrEpt; ++v) {
+      const int64_t e = base + (int64_t)v * kErrThreads;
+      if (e < total) {
+        const int64_t r = e / N, c = e - r * N;
+        const double d = (double)C[k * strideC + r * ldc + c] - Ref[r * ldr + c];
+        d2 += d * d;
+      }
+    }
+    const double s = block_sum(d2, sm[it & 1]);
+    if (threadIdx.x == 0) part[k * nblk + blockIdx.x] = s;
+  }
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(kErrThreads)
+    err_average_kernel(const TC* C, int64_t K, int64_t N, int64_t ldc, int64_t strideC, const double* Ref,
+                       int64_t ldr, double* part, int64_t nblk) {
+  __shared__ double sm[2][kErrThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kErrPer + threadIdx.x, total = N * N;
+  int64_t off[kErrEpt];
+  double ref[kErrEpt], sum[kErrEpt];
+  TC next[kErrEpt];
+#pragma unroll
+  for (int v = 0; v < kErrEpt; ++v) {
+    const int64_t e = base + (int64_t)v * kErrThreads;
+    const bool in = e < total;
+    const int64_t r = in ? e / N : 0, c = in ? e - r * N : 0;
+    off[v] = in ? r * ldc + c : -1;
+    ref[v] = in ? Ref[r * ldr + c] : 0.0;
+    sum[v] = 0.0;
+    next[v] = off[v] >= 0 && K > 0 ? C[off[v]] : (TC)0;
+  }
+  for (int64_t n = 0; n < K; ++n) {
+    TC cur[kErrEpt];
+#pragma unroll
+    for (int v = 0; v < kErrEpt; ++v) {
+      cur[v] = next[v];
+      // prefetch realization n + 1 while this one is reduced
+      next[v] = (off[v] >= 0 && n + 1 < K) ? C[(n + 1) * strideC + off[v]] : (TC)0;
+    }
+    const double inv = 1.0 / (double)(n + 1);
+    double d2 = 0.0;
+#pragma unroll
+    for (int v = 0; v < kErrEpt; ++v) {
+      if (off[v] < 0) continue;
+      sum[v] += (double)cur[v];
+      const double d = sum[v] * inv - ref[v];
+      d2 += d * d;
+    }
+    const double s = block_sum(d2, sm[n & 1]);
+    if (threadIdx.x == 0) part[n * nblk + blockIdx.x] = s;
+  }
+}
+
+// err[k] = sqrt(sum_b part[k][b]) / ||Ref||, ||Ref||^2 from the norm partials in CTA order.
+__global__ void __launch_bounds__(kErrThreads)
+    err_final_kernel(const double* part, int64_t K, int64_t nblk, const double* ref_part, int nref, double* err) {
+  __shared__ double sm[kErrThreads / 32];
+  __shared__ double ref2;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nref; i += kErrThreads) a += ref_part[2 * i];
+  const double s = block_sum(a, sm);
+  if (threadIdx.x == 0) ref2 = s;
+  __syncthreads();
+  const double rn = sqrt(ref2);
+  for (int64_t k = threadIdx.x; k < K; k += kErrThreads) {
+    double t = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) t += part[k * nblk + b];
+    err[k] = sqrt(t) / rn;
+  }
+}
+
+inline int64_t err_blocks(int64_t N) { return (N * N + kErrPer - 1) / kErrPer; }
+
 }  // namespace
 }  // namespace rbc
 
 using namespace rbc;
+
+extern "C" size_t rbc_realization_errors_work_size(int64_t K, int64_t N) {
+  if (K < 0 || N < 0) return 0;
+  return sizeof(double) * ((size_t)K * (size_t)err_blocks(N) + 2 * kNormBlocks);
+}
+
+extern "C" rbc_status rbc_realization_errors(const void* C, int ct, int64_t K, int64_t N, int64_t ldc,
+                                             int64_t strideC, const double* Ref, int64_t ldr, int mode, double* err,
+                                             void* work, size_t work_bytes, void* stream) {
+  if (!C || !Ref || !err || !work) return fail(RBC_EINVAL, "null argument");
+  if (K < 1 || N < 1 || ldc < N || ldr < N || (K > 1 && strideC < ldc * N))
+    return fail(RBC_EINVAL, "bad shape: K, N >= 1, ldc, ldr >= N, strideC >= ldc * N");
+  if (ct != RBC_IO_F32 && ct != RBC_IO_F64) return fail(RBC_EINVAL, "bad dtype");
+  if (mode != RBC_ERR_EACH && mode != RBC_ERR_AVERAGE) return fail(RBC_EINVAL, "bad error mode");
+  if (work_bytes < rbc_realization_errors_work_size(K, N)) return fail(RBC_ENOMEM, "error workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nblk = err_blocks(N);
+  if (nblk > 0x7fffffff) return fail(RBC_EINVAL, "N too large");
+  double* part = static_cast<double*>(work);
+  double* ref_part = part + K * nblk;
+  norm_partial_kernel<double, double><<<kNormBlocks, kNormThreads, 0, st>>>(Ref, (const double*)nullptr, N, N, ldr,
+                                                                             0, ref_part);
+  if (mode == RBC_ERR_EACH) {
+    const dim3 grid((unsigned)nblk, (unsigned)(K < 65535 ? K : 65535));
+    if (ct == RBC_IO_F32)
+      err_each_kernel<float><<<grid, kErrThreads, 0, st>>>(static_cast<const float*>(C), K, N, ldc, strideC, Ref,
+                                                           ldr, part, nblk);
+    else
+      err_each_kernel<double><<<grid, kErrThreads, 0, st>>>(static_cast<const double*>(C), K, N, ldc, strideC,
+                                                            Ref, ldr, part, nblk);
+  } else {
+    if (ct == RBC_IO_F32)
+      err_average_kernel<float><<<(unsigned)nblk, kErrThreads, 0, st>>>(static_cast<const float*>(C), K, N, ldc,
+                                                                        strideC, Ref, ldr, part, nblk);
+    else
+      err_average_kernel<double><<<(unsigned)nblk, kErrThreads, 0, st>>>(static_cast<const double*>(C), K, N, ldc,
+                                                                         strideC, Ref, ldr, part, nblk);
+  }
+  err_final_kernel<<<1, kErrThreads, 0, st>>>(part, K, nblk, ref_part, kNormBlocks, err);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+}
 
 extern "C" size_t rbc_norms_work_size(void) { return sizeof(double) * 2 * kNormBlocks; }
 

@@ -19,6 +19,7 @@ IO_F64, IO_F32 = 0, 1
 LEAF_F64, LEAF_F32, LEAF_TF32, LEAF_BF16, LEAF_F16, LEAF_3XBF16, LEAF_3XTF32 = range(7)
 RAND_FULL, RAND_SIGN, RAND_PERM, RAND_NONE = range(4)
 DRAW_PER_NODE, DRAW_PER_LEVEL = 0, 1
+ERR_EACH, ERR_AVERAGE = 0, 1
 LEAF_NAMES = {"f64": LEAF_F64, "f32": LEAF_F32, "tf32": LEAF_TF32, "bf16": LEAF_BF16,
               "f16": LEAF_F16, "3xbf16": LEAF_3XBF16, "3xtf32": LEAF_3XTF32}
 
@@ -97,6 +98,12 @@ SIGNATURES = {
     "rbc_norms": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P,
                             C.c_size_t, _P]),
     "rbc_norms_work_size": (C.c_size_t, []),
+    "rbc_realizations_workspace_size": (C.c_size_t, [_P, C.c_int64, C.c_int, C.c_int, C.c_int64]),
+    "rbc_matmul_realizations": (C.c_int, [C.POINTER(_P), C.c_int64, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64,
+                                          C.c_int64, C.c_int64, C.c_int, C.c_int, _P, C.c_size_t, _P]),
+    "rbc_realization_errors": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int64,
+                                         C.c_int, _P, _P, C.c_size_t, _P]),
+    "rbc_realization_errors_work_size": (C.c_size_t, [C.c_int64, C.c_int64]),
     "rbc_status_string": (C.c_char_p, [C.c_int]),
     "rbc_last_error": (C.c_char_p, []),
     "rbc_version": (C.c_int, []),
@@ -247,6 +254,51 @@ def norms(X, Y=None, stream=None, work=None, out=None):
                           X.stride(0), Y.stride(0) if Y is not None else 0, _io_of(X), yt,
                           out.data_ptr(), work.data_ptr(), work.numel(), _stream_ptr(stream)),
           "rbc_norms")
+    return out
+
+
+def realizations(plans, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, stream=None, batch=None):
+    """K independent realizations through rbc_matmul_realizations: realization k uses plans[k];
+    returns (or fills) a K x N x N tensor.  `batch` bounds how many realizations share the
+    workspace at once (default: all)."""
+    import torch
+    K, N = len(plans), A.shape[0]
+    if A.shape != (N, N) or B.shape != (N, N) or A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("square N x N inputs with unit column stride required")
+    io = _io_of(A)
+    if _io_of(B) != io:
+        raise TypeError("A and B must have the same dtype")
+    if C_out is None:
+        C_out = torch.empty((K, N, N), dtype=A.dtype, device=A.device)
+    if C_out.shape != (K, N, N) or C_out.stride(2) != 1:
+        raise ValueError("C_out must be K x N x N with unit column stride")
+    if workspace is None:
+        b = K if batch is None else max(1, min(K, batch))
+        need = int(lib().rbc_realizations_workspace_size(plans[0].handle, N, io, leaf, b))
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
+    handles = (_P * K)(*[p.handle.value for p in plans])
+    check(lib().rbc_matmul_realizations(handles, K, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), N, A.stride(0),
+                                        B.stride(0), C_out.stride(1), C_out.stride(0), io, leaf,
+                                        workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)),
+          "rbc_matmul_realizations")
+    return C_out
+
+
+def realization_errors(Cs, Ref, mode: int = ERR_EACH, stream=None, work=None, out=None):
+    """Relative Frobenius errors of the K x N x N realizations Cs against the fp64 reference
+    Ref (rbc_realization_errors): per realization (ERR_EACH) or of the running average
+    (ERR_AVERAGE).  Returns a K-element float64 CUDA tensor."""
+    import torch
+    K, N, _ = Cs.shape
+    if Ref.dtype != torch.float64 or Ref.shape != (N, N) or Ref.stride(1) != 1 or Cs.stride(2) != 1:
+        raise ValueError("Ref must be an N x N float64 tensor; Cs and Ref need unit column stride")
+    if out is None:
+        out = torch.empty(K, dtype=torch.float64, device=Cs.device)
+    if work is None:
+        work = torch.empty(int(lib().rbc_realization_errors_work_size(K, N)), dtype=torch.uint8, device=Cs.device)
+    check(lib().rbc_realization_errors(Cs.data_ptr(), _io_of(Cs), K, N, Cs.stride(1), Cs.stride(0), Ref.data_ptr(),
+                                       Ref.stride(0), mode, out.data_ptr(), work.data_ptr(), work.numel(),
+                                       _stream_ptr(stream)), "rbc_realization_errors")
     return out
 
 
