@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--decode", type=int, default=0, help="0 auto, 1 fused, 2 staged")
     ap.add_argument("--no-errors", action="store_true", help="skip the error pass after the timing")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "experiments"],
                     help="sweep: the at-scale fp32 sweep (default); batch: 512 uneven instances in one "
                          "grouped leaf launch replayed from a CUDA graph")
     ap.add_argument("--instances", type=int, default=512)
@@ -549,6 +549,154 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+# Section 3's two experiment shapes: (figure, formula, io, N, Q, realizations, inputs)
+EXP_CONFIGS = [("fig2", "noisy-strassen", "f64", 80, 3, 10_000, "normal"),
+               ("fig5", "strassen", "f32", 320, 5, 100, "adv3")]
+
+
+def _exp_setup(dev):
+    import numpy as np
+
+    import paper_1905_07439_gb300 as rbc
+    from paper_1905_07439_gb300 import experiments as ex
+    from rbc_inputs import formula_by_name
+    from rbc_inputs.matrices import matrix_pair
+
+    import torch
+    out = []
+    for fig, fname, io, N, Q, K, dist in EXP_CONFIGS:
+        U, V, W = formula_by_name(fname, seed=0)
+        A, B = matrix_pair(dist, N, 1000)
+        run = ex.Runner(U, V, W, A, B, io, device=str(dev))
+        plan = run.plan(Q, rbc.RAND_FULL, rbc.DRAW_PER_LEVEL)
+        seeds = np.arange(K, dtype=np.uint64) + (Q << 24)
+        one = int(rbc.lib().rbc_realizations_workspace_size(plan.handle, N, run.io, run.leaf, 1))
+        batch = max(1, min(K, (8 << 30) // one))
+        ws = torch.empty(int(rbc.lib().rbc_realizations_workspace_size(plan.handle, N, run.io, run.leaf, batch)),
+                         dtype=torch.uint8, device=dev)
+        Cs = torch.empty((K, N, N), dtype=run.dtype, device=dev)
+        err = torch.empty(K, dtype=torch.float64, device=dev)
+        work = torch.empty(int(rbc.lib().rbc_realization_errors_work_size(K, N)), dtype=torch.uint8, device=dev)
+        mode = rbc.ERR_AVERAGE if fig == "fig2" else rbc.ERR_EACH
+        out.append(dict(fig=fig, fname=fname, io=io, N=N, Q=Q, K=K, dist=dist, run=run, plan=plan, seeds=seeds,
+                        ws=ws, Cs=Cs, err=err, work=work, mode=mode, A=A, B=B, batch=batch))
+    return out
+
+
+def _exp_step(cfgs, stream, host=None):
+    """One step: every configuration's realizations and their error reduction.  With `host`,
+    A and B are copied from pinned host memory first and the errors back after."""
+    import paper_1905_07439_gb300 as rbc
+    for i, c in enumerate(cfgs):
+        r = c["run"]
+        if host is not None:
+            r.A.copy_(host[i]["A"], non_blocking=True)
+            r.B.copy_(host[i]["B"], non_blocking=True)
+        rbc.realizations(c["plan"], c["seeds"], r.A, r.B, c["Cs"], leaf=r.leaf, workspace=c["ws"], stream=stream)
+        rbc.realization_errors(c["Cs"], r.ref, c["mode"], stream=stream, work=c["work"], out=c["err"])
+        if host is not None:
+            host[i]["err"].copy_(c["err"], non_blocking=True)
+
+
+def exp_cpu_baseline(cfg, budget_s=12.0):
+    """The oracle on the host cores: realizations of the Figure 2 shape (perturbed Strassen,
+    N = 80, Q = 3, fp64) and their error, until about `budget_s` seconds."""
+    import numpy as np
+
+    from oracle import rbc_oracle as o
+    from rbc_inputs import formula_by_name
+    U, V, W = formula_by_name(cfg["fname"], seed=0)
+    A, B = cfg["A"], cfg["B"]
+    AB = A @ B
+    t0 = time.perf_counter()
+    n, acc, errs = 0, np.zeros_like(AB), []
+    while time.perf_counter() - t0 < budget_s:
+        C = o.rbc(A, B, o.Plan(U, V, W, levels=cfg["Q"], seed=int(cfg["seeds"][n]), mode=o.RAND_FULL,
+                              scope=o.DRAW_PER_LEVEL))
+        acc += C
+        n += 1
+        errs.append(float(np.linalg.norm(acc / n - AB) / np.linalg.norm(AB)))
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 3), "unit": "realizations/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} realizations of {cfg['fname']} N={cfg['N']} Q={cfg['Q']} fp64 per-level draws "
+                      f"with their error of average ({dt:.1f} s, numpy fp64)",
+            "errors": errs}
+
+
+def run_experiments(args):
+    """Section 3 experiment shapes: realizations per second (all realizations of both
+    configurations, with their error reductions, per step)."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfgs = _exp_setup(dev)
+    stream = torch.cuda.Stream(dev)
+    for _ in range(max(3, args.warmup)):
+        _exp_step(cfgs, stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            _exp_step(cfgs, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    per_step = sum(c["K"] for c in cfgs)
+    # per configuration, one step each
+    parts = []
+    for c in cfgs:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _exp_step([c], stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e = c["err"].cpu().numpy()
+        parts.append({"figure": c["fig"], "formula": c["fname"], "io": c["io"], "N": c["N"], "Q": c["Q"],
+                      "realizations": c["K"], "inputs": c["dist"], "batch": c["batch"],
+                      "ms": round(a.elapsed_time(b), 3),
+                      "realizations_per_s": round(c["K"] / (a.elapsed_time(b) * 1e-3), 1),
+                      "error": ({"first": float(e[0]), "last": float(e[-1])} if c["mode"] == 1 else
+                                {"median": float(np.median(e)), "min": float(e.min()), "max": float(e.max())})})
+    # end to end: inputs from pinned host memory, errors back to the host, every step
+    host = [{"A": c["run"].A.cpu().pin_memory(), "B": c["run"].B.cpu().pin_memory(),
+             "err": torch.empty(c["K"], dtype=torch.float64).pin_memory()} for c in cfgs]
+    _exp_step(cfgs, stream, host)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _exp_step(cfgs, stream, host)
+    stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = sum(h["A"].numel() * h["A"].element_size() * 2 for h in host)
+    d2h = sum(h["err"].numel() * 8 for h in host)
+    line = {
+        "metric": "Section 3 realizations/s (realizations + error reductions)", "value":
+            round(world * per_step / (ms * 1e-3), 1), "unit": "realizations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (fig2 shape), f32 (fig5 shape)",
+        "data": "synthetic (seeded N(0,1); type-3 adversarial)",
+        "config": {"workload": "rbc-experiments: 10^4 realizations of perturbed Strassen N=80 Q=3 fp64 with the "
+                               "error of their running average + 100 realizations of Strassen N=320 Q=5 fp32 "
+                               "on adversarial type-3 inputs with per-realization errors; per-level draws",
+                   "parallelism": f"replicas x{world}", "l2": "outputs of each step (0.6 GB) exceed L2"},
+        "parts": parts,
+        "e2e": {"value": round(world * per_step / e2e_s, 1), "unit": "realizations/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = exp_cpu_baseline(cfgs[0])
+        ce = line["cpu_baseline"].pop("errors")
+        g = cfgs[0]["err"].cpu().numpy()[: len(ce)]
+        line["cpu_baseline"]["parity_error_of_average_max_rel_diff"] = float(np.max(np.abs(g - ce) / np.abs(ce)))
+    if rank == 0:
+        print(json.dumps(line))
+
+
 SERVE_LEAF = {"fp32": "3xbf16", "bf16-leaf": "bf16", "3xbf16-leaf": "3xbf16"}
 
 
@@ -690,6 +838,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "experiments":
+        run_experiments(args)
     else:
         run_ours(args)
 

@@ -175,23 +175,25 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
                          void* workspace, size_t workspace_bytes, void* stream,
                          rbc_matmul_opts* opts);
 
-/* Independent realizations F^(L)_1 .. F^(L)_K of the same product (Section 3: the error of
- * an average of realizations, Eq. error-of-average, and the spread of single realizations,
- * Eq. average-of-error).  Realization k uses plans[k] (its draws); every plan must describe
- * the same computation otherwise (U, V, W, R, n0, levels, rand_mode, draw_scope, rescaling:
- * RBC_EINVAL if not).  A, B: device, N x N, shared by all realizations.  Output k:
- * C + k * strideC (elements; strideC >= ldc * N when count > 1), N x N with leading dim ldc.
- * The draws of as many realizations as the workspace holds are processed by each launch
- * (staged decode); rbc_realizations_workspace_size(plan, N, io, leaf, count) is the
- * workspace that holds all of them at once, and any workspace of at least the size for
- * count = 1 works (the realizations then run in consecutive batches on the stream).
- * Leaf modes and dtypes as rbc_matmul.  L = 0 computes the same standard product K times. */
+/* Independent realizations F^(L)_1 .. F^(L)_K of one plan's product (Section 3: the error
+ * of an average of realizations, Eq. error-of-average, and the spread of single
+ * realizations, Eq. average-of-error).  Realization k is the plan's computation with its
+ * draws taken from seed seeds[k] instead of the plan's own (the same draws a plan created
+ * with that seed has; seeds[k] == the plan's seed reuses its draws).  A, B: device, N x N,
+ * shared by all realizations.  Output k: C + k * strideC (elements; strideC >= ldc * N when
+ * count > 1), N x N with leading dim ldc.  As many realizations as the workspace holds run
+ * together, their encode/decode passes batched across realizations (staged decode) and their
+ * leaf products in one launch; rbc_realizations_workspace_size(plan, N, io, leaf, count) is
+ * the workspace that holds `count` at once, and any workspace of at least the size for
+ * count = 1 works (batches then follow one another on the stream).  Leaf modes and dtypes
+ * as rbc_matmul.  L = 0 computes the same standard product K times. */
 size_t rbc_realizations_workspace_size(rbc_plan_t plan, int64_t N, int io_dtype, int leaf_dtype,
                                        int64_t count);
-rbc_status rbc_matmul_realizations(const rbc_plan_t* plans, int64_t count, const void* A,
-                                   const void* B, void* C, int64_t N, int64_t lda, int64_t ldb,
-                                   int64_t ldc, int64_t strideC, int io_dtype, int leaf_dtype,
-                                   void* workspace, size_t workspace_bytes, void* stream);
+rbc_status rbc_matmul_realizations(rbc_plan_t plan, const uint64_t* seeds, int64_t count,
+                                   const void* A, const void* B, void* C, int64_t N, int64_t lda,
+                                   int64_t ldb, int64_t ldc, int64_t strideC, int io_dtype,
+                                   int leaf_dtype, void* workspace, size_t workspace_bytes,
+                                   void* stream);
 
 /* Relative Frobenius errors of K realizations against a reference product (Section 3),
  * in fp64 with a fixed summation order (bit-identical on repeated calls):

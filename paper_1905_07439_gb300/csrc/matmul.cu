@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <memory>
+#include <vector>
 
 #include "convert.cuh"
 #include "level_kernels.cuh"
@@ -163,7 +164,7 @@ int64_t launch_draws(const rbc_plan_s* p, int g, int64_t cnt) {
 // one realization at a time, its parents chunked.
 template <class F>
 rbc_status for_each_launch(const Reals& rs, int d, int g, F&& f) {
-  const rbc_plan_s* p = rs.plans[0];
+  const rbc_plan_s* p = rs.plan;
   const int64_t P = ipow(p->R, d);
   const int64_t D = launch_draws(p, g, P);
   if (D <= kMaxDraws) {
@@ -188,7 +189,7 @@ rbc_status for_each_launch(const Reals& rs, int d, int g, F&& f) {
 template <typename T>
 rbc_status launch_tables(const Reals& rs, int d, int g, int64_t k0, int64_t kc, int64_t c0, int64_t cnt, PassArgs* a,
                          Tables<T>& tab) {
-  const rbc_plan_s* p = rs.plans[k0];
+  const rbc_plan_s* p = rs.plan;
   rbc_status s = fill_tables(p, 0, 0, &tab);
   if (s != RBC_OK) return s;
   a->depth = d;
@@ -215,9 +216,9 @@ rbc_status launch_tables(const Reals& rs, int d, int g, int64_t k0, int64_t kc, 
   a->real_draws = per;
   int64_t o = 0;
   for (int64_t k = 0; k < kc; ++k) {
-    const rbc_plan_s* q = rs.plans[k0 + k];
+    const uint64_t* q = rs.draws + (k0 + k) * p->draw_count;
     for (int i = 0; i < nr; ++i)
-      for (int64_t e = 0; e < count[i]; ++e) tab.draw[o++] = q->packed[first[i] + e];
+      for (int64_t e = 0; e < count[i]; ++e) tab.draw[o++] = q[first[i] + e];
   }
   return RBC_OK;
 }
@@ -227,7 +228,7 @@ rbc_status launch_tables(const Reals& rs, int d, int g, int64_t k0, int64_t kc, 
 template <typename T>
 rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor, const void* X, int64_t ldx,
                           char* ws, Tables<T>& tab, cudaStream_t st) {
-  const rbc_plan_s* p = rs.plans[0];
+  const rbc_plan_s* p = rs.plan;
   const int L = p->L, R = p->R, n0 = p->n0;
   const size_t* enc = tensor == 0 ? lo.encA : lo.encB;
   char* leafbuf = ws + (tensor == 0 ? lo.leafS : lo.leafT);
@@ -303,7 +304,7 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
 template <typename T>
 rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc, char* ws, Tables<T>& tab,
                          cudaStream_t st) {
-  const rbc_plan_s* p = rs.plans[0];
+  const rbc_plan_s* p = rs.plan;
   const int L = p->L, R = p->R, n0 = p->n0;
   for (int i = lo.passes.count - 1; i >= 0; --i) {
     const int d = lo.passes.top[i], g = lo.passes.g[i];
@@ -355,7 +356,7 @@ rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, 
                const rbc_matmul_opts* opts) {
   static thread_local TablesBox<T> box;
   Tables<T>& tab = *box.t;
-  const rbc_plan_s* p = rs.plans[0];
+  const rbc_plan_s* p = rs.plan;
   mark(opts, 0, st);
   rbc_status s = encode_operand<T>(rs, lo, io, 0, A, lda, ws, tab, st);
   if (s != RBC_OK) return s;
@@ -474,22 +475,13 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
     cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);  // clear the status word
     if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
   }
-  const Reals rs{&plan, 1, 0};
+  const Reals rs{plan, plan->packed.data(), 1, 0};
   if (io == RBC_IO_F64)
     s = run<double>(rs, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
   else
     s = run<float>(rs, lo, A, B, C, N, lda, ldb, ldc, io, leaf, ws, st, opts);
   if (opts) opts->launches = g_launches;
   return s;
-}
-
-// The plans of a realization batch must describe the same computation up to their draws.
-static rbc_status same_computation(const rbc_plan_s* a, const rbc_plan_s* b) {
-  if (!b) return fail(RBC_EINVAL, "null plan in the realization list");
-  if (a->R != b->R || a->n0 != b->n0 || a->L != b->L || a->mode != b->mode || a->scope != b->scope ||
-      a->scale != b->scale || a->U != b->U || a->V != b->V || a->W != b->W)
-    return fail(RBC_EINVAL, "realization plans differ in formula, depth, mode, scope or rescaling");
-  return RBC_OK;
 }
 
 size_t rbc_realizations_workspace_size(rbc_plan_t plan, int64_t N, int io, int leaf, int64_t count) {
@@ -500,53 +492,59 @@ size_t rbc_realizations_workspace_size(rbc_plan_t plan, int64_t N, int io, int l
   return lo.total;
 }
 
-rbc_status rbc_matmul_realizations(const rbc_plan_t* plans, int64_t count, const void* A, const void* B, void* C,
-                                   int64_t N, int64_t lda, int64_t ldb, int64_t ldc, int64_t strideC, int io,
-                                   int leaf, void* workspace, size_t ws_bytes, void* stream) {
-  if (!plans || count < 1 || !A || !B || !C) return fail(RBC_EINVAL, "null argument or empty realization list");
-  const rbc_plan_s* p0 = plans[0];
-  if (!p0) return fail(RBC_EINVAL, "null plan in the realization list");
-  for (int64_t k = 1; k < count; ++k) {
-    rbc_status s = same_computation(p0, plans[k]);
-    if (s != RBC_OK) return s;
-  }
+rbc_status rbc_matmul_realizations(rbc_plan_t plan, const uint64_t* seeds, int64_t count, const void* A,
+                                   const void* B, void* C, int64_t N, int64_t lda, int64_t ldb, int64_t ldc,
+                                   int64_t strideC, int io, int leaf, void* workspace, size_t ws_bytes,
+                                   void* stream) {
+  if (!plan || !seeds || count < 1 || !A || !B || !C)
+    return fail(RBC_EINVAL, "null argument or empty realization list");
   if (lda < N || ldb < N || ldc < N) return fail(RBC_EINVAL, "leading dimension smaller than N");
   if (count > 1 && strideC < ldc * N) return fail(RBC_EINVAL, "strideC smaller than ldc * N: outputs overlap");
   if (!workspace || ((uintptr_t)workspace & 255))
     return fail(RBC_EINVAL, "workspace must be a 256-byte aligned device pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t es = io == RBC_IO_F64 ? 8 : 4;
-  if (p0->L == 0) {  // the classical product: every realization is the same computation
+  if (plan->L == 0) {  // the standard product: no draws, every realization is the same
     for (int64_t k = 0; k < count; ++k) {
-      rbc_status s = rbc_matmul_ex(plans[k], A, B, static_cast<char*>(C) + (size_t)k * strideC * es, N, lda, ldb,
-                                   ldc, io, leaf, workspace, ws_bytes, stream, nullptr);
+      rbc_status s = rbc_matmul_ex(plan, A, B, static_cast<char*>(C) + (size_t)k * strideC * es, N, lda, ldb, ldc,
+                                   io, leaf, workspace, ws_bytes, stream, nullptr);
       if (s != RBC_OK) return s;
     }
     return RBC_OK;
   }
   Layout one;
-  rbc_status s = make_layout(p0, N, io, leaf, 2, &one, 1);
+  rbc_status s = make_layout(plan, N, io, leaf, 2, &one, 1);
   if (s != RBC_OK) return s;
   if (ws_bytes < one.total) return fail(RBC_ENOMEM, "workspace smaller than one realization needs");
   // The largest batch whose layout fits: a batch of b needs at most kStatusBytes + b * (one
   // realization's bytes beyond the status words).
   const size_t per = one.total - kStatusBytes;
-  int64_t batch = (int64_t)std::min<size_t>((size_t)count, (ws_bytes - kStatusBytes) / per);
+  const int64_t batch = (int64_t)std::min<size_t>((size_t)count, (ws_bytes - kStatusBytes) / per);
   Layout lo;
-  s = make_layout(p0, N, io, leaf, 2, &lo, batch);
+  s = make_layout(plan, N, io, leaf, 2, &lo, batch);
   if (s != RBC_OK) return s;
+  std::vector<uint64_t> draws;
+  try {
+    draws.resize((size_t)(batch * plan->draw_count));
+  } catch (...) {
+    return fail(RBC_ENOMEM, "out of host memory for the draws of a batch");
+  }
   char* ws = static_cast<char*>(workspace);
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int), st);
   if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
   for (int64_t k0 = 0; k0 < count; k0 += batch) {
     const int64_t kc = std::min(batch, count - k0);
     Layout lk;
-    s = kc == batch ? RBC_OK : make_layout(p0, N, io, leaf, 2, &lk, kc);
-    if (s != RBC_OK) return s;
-    const Reals rs{plans + k0, kc, strideC};
+    if (kc != batch) {
+      s = make_layout(plan, N, io, leaf, 2, &lk, kc);
+      if (s != RBC_OK) return s;
+    }
+    for (int64_t k = 0; k < kc; ++k) packed_draws(plan, seeds[k0 + k], draws.data() + k * plan->draw_count);
+    const Reals rs{plan, draws.data(), kc, strideC};
     void* Ck = static_cast<char*>(C) + (size_t)k0 * strideC * es;
-    s = io == RBC_IO_F64 ? run<double>(rs, kc == batch ? lo : lk, A, B, Ck, N, lda, ldb, ldc, io, leaf, ws, st, nullptr)
-                         : run<float>(rs, kc == batch ? lo : lk, A, B, Ck, N, lda, ldb, ldc, io, leaf, ws, st, nullptr);
+    const Layout& l = kc == batch ? lo : lk;
+    s = io == RBC_IO_F64 ? run<double>(rs, l, A, B, Ck, N, lda, ldb, ldc, io, leaf, ws, st, nullptr)
+                         : run<float>(rs, l, A, B, Ck, N, lda, ldb, ldc, io, leaf, ws, st, nullptr);
     if (s != RBC_OK) return s;
   }
   return RBC_OK;

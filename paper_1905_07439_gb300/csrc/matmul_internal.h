@@ -38,11 +38,13 @@ struct Layout {
   size_t total = 0;
 };
 
-// Independent realizations computed together: plans[k], k < count, which share the formula,
-// depth, randomization mode, draw scope and rescaling and differ in their draws.  Their
-// intermediates sit realization-major in one workspace; output k is C + k * strideC.
+// Independent realizations of one plan's computation computed together, differing only in
+// their draws: realization k's draw sets (plan->draw_count words, heap or level order) are
+// at draws + k * plan->draw_count.  Their intermediates sit realization-major in one
+// workspace; output k is C + k * strideC.
 struct Reals {
-  const rbc_plan_s* const* plans = nullptr;
+  const rbc_plan_s* plan = nullptr;
+  const uint64_t* draws = nullptr;
   int64_t count = 1;
   int64_t strideC = 0;  // elements
 };
@@ -62,13 +64,13 @@ rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc
 template <typename T>
 inline rbc_status encode_operand(const rbc_plan_s* p, const Layout& lo, int io, int tensor, const void* X,
                                  int64_t ldx, char* ws, Tables<T>& tab, cudaStream_t st) {
-  const Reals rs{&p, 1, 0};
+  const Reals rs{p, p->packed.data(), 1, 0};
   return encode_operand<T>(rs, lo, io, tensor, X, ldx, ws, tab, st);
 }
 template <typename T>
 inline rbc_status decode_passes(const rbc_plan_s* p, const Layout& lo, void* C, int64_t ldc, char* ws,
                                 Tables<T>& tab, cudaStream_t st) {
-  const Reals rs{&p, 1, 0};
+  const Reals rs{p, p->packed.data(), 1, 0};
   return decode_passes<T>(rs, lo, C, ldc, ws, tab, st);
 }
 

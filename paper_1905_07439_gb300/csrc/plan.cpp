@@ -41,16 +41,16 @@ static void draw_permutation(uint64_t w, int n0, int* p) {
   }
 }
 
-static void draw_set(const rbc_plan_s* pl, uint64_t key, int pi[3][kMaxN0], int s[3][kMaxN0]) {
+static void draw_set(const rbc_plan_s* pl, uint64_t seed, uint64_t key, int pi[3][kMaxN0], int s[3][kMaxN0]) {
   const bool perm = pl->mode == RBC_RAND_FULL || pl->mode == RBC_RAND_PERM;
   const bool sign = pl->mode == RBC_RAND_FULL || pl->mode == RBC_RAND_SIGN;
   for (int c = 0; c < 3; ++c) {
     if (perm) {
-      draw_permutation(stream_word(pl->seed, key, (uint64_t)c), pl->n0, pi[c]);
+      draw_permutation(stream_word(seed, key, (uint64_t)c), pl->n0, pi[c]);
     } else {
       for (int j = 0; j < pl->n0; ++j) pi[c][j] = j;
     }
-    const uint64_t w = stream_word(pl->seed, key, (uint64_t)(3 + c));
+    const uint64_t w = stream_word(seed, key, (uint64_t)(3 + c));
     for (int j = 0; j < pl->n0; ++j) s[c][j] = (sign && ((w >> j) & 1u)) ? -1 : 1;
   }
 }
@@ -104,6 +104,18 @@ static double formula_gamma(const rbc_plan_s* p) {
     acc += u * v * w;
   }
   return std::sqrt(acc);
+}
+
+void packed_draws(const rbc_plan_s* p, uint64_t seed, uint64_t* out) {
+  if (seed == p->seed) {
+    for (int64_t key = 0; key < p->draw_count; ++key) out[key] = p->packed[key];
+    return;
+  }
+  for (int64_t key = 0; key < p->draw_count; ++key) {
+    int pi[3][kMaxN0], s[3][kMaxN0];
+    draw_set(p, seed, (uint64_t)key, pi, s);
+    out[key] = pack_draw(pi, s, p->n0);
+  }
 }
 
 template <typename T>
@@ -213,7 +225,7 @@ rbc_status rbc_plan_create_ex(const rbc_plan_desc* d, rbc_plan_t* out) {
   }
   for (int64_t key = 0; key < draws; ++key) {
     int pi[3][kMaxN0], s[3][kMaxN0];
-    draw_set(p, (uint64_t)key, pi, s);
+    draw_set(p, p->seed, (uint64_t)key, pi, s);
     p->packed[key] = pack_draw(pi, s, d->n0);
     for (int c = 0; c < 3; ++c)
       for (int j = 0; j < d->n0; ++j) {

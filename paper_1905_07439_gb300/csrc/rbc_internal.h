@@ -83,6 +83,9 @@ inline int64_t ipow(int64_t b, int e) {
   return r;
 }
 
+// The packed draw sets of plan p's computation under another seed (p->draw_count words).
+void packed_draws(const rbc_plan_s* p, uint64_t seed, uint64_t* out);
+
 // Fill the tables of a launch touching draw sets [key_first, key_first + count).
 template <typename T>
 rbc_status fill_tables(const rbc_plan_s* p, int64_t key_first, int64_t count, Tables<T>* t);

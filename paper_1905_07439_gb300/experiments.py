@@ -14,7 +14,7 @@ entry equal to 1 and on five zero entries per tensor) in double precision; Secti
 the exact Strassen formula in single precision, with the fully randomized, random-sign,
 random-permutation and deterministic variants, on Gaussian, uniform, adversarial (types 1-3)
 and Hilbert inputs.  Draws are per level, as the paper defines them (one draw set per
-recursion level shared by its nodes); realization i uses seed base + i.
+recursion level shared by its nodes); realization i draws from seed base + i.
 
 Every realization, reference product and error norm is computed by the library's kernels:
 all realizations of one configuration in batched launches (rbc_matmul_realizations), the
@@ -81,20 +81,21 @@ class Runner:
         p0 = rbc.Plan(U, V, W, levels=0, seed=0, rand_mode=rbc.RAND_NONE)
         self.ref = rbc.matmul(p0, self.A64, self.B64, leaf=rbc.LEAF_F64)
 
-    def plans(self, levels: int, mode: int, count: int, seed: int, scope: int):
-        return [rbc.Plan(self.U, self.V, self.W, levels=levels, seed=seed + i, rand_mode=mode, draw_scope=scope)
-                for i in range(count)]
+    def plan(self, levels: int, mode: int, scope: int):
+        return rbc.Plan(self.U, self.V, self.W, levels=levels, seed=0, rand_mode=mode, draw_scope=scope)
 
-    def realize(self, plans, leaf=None, max_ws_bytes: int = 8 << 30):
+    def realize(self, plan, seeds, leaf=None, max_ws_bytes: int = 8 << 30):
+        """Realizations of `plan` with draws from each seed, batched as far as `max_ws_bytes`
+        of workspace allows."""
         torch = self.torch
         leaf = self.leaf if leaf is None else leaf
-        one = int(rbc.lib().rbc_realizations_workspace_size(plans[0].handle, self.N, self.io, leaf, 1))
+        one = int(rbc.lib().rbc_realizations_workspace_size(plan.handle, self.N, self.io, leaf, 1))
         if one == 0:
             raise rbc.RbcError(rbc.RBC_EINVAL, "no layout for this configuration")
-        batch = max(1, min(len(plans), max_ws_bytes // one))
-        need = int(rbc.lib().rbc_realizations_workspace_size(plans[0].handle, self.N, self.io, leaf, batch))
+        batch = max(1, min(len(seeds), max_ws_bytes // one))
+        need = int(rbc.lib().rbc_realizations_workspace_size(plan.handle, self.N, self.io, leaf, batch))
         ws = torch.empty(need, dtype=torch.uint8, device=self.A.device)
-        return rbc.realizations(plans, self.A, self.B, leaf=leaf, workspace=ws)
+        return rbc.realizations(plan, seeds, self.A, self.B, leaf=leaf, workspace=ws)
 
     def errors(self, Cs, mode: int):
         return rbc.realization_errors(Cs, self.ref, mode).cpu().numpy()
@@ -144,13 +145,14 @@ def run_experiment(name: str, K: int = 10_000, trials: int = 100, seed: int = 0,
         for Q in lv:
             if N % (2 ** Q):
                 continue
-            det = run.realize(run.plans(Q, rbc.RAND_NONE, 1, seed, scope), leaf_id)
+            det = run.realize(run.plan(Q, rbc.RAND_NONE, scope), [0], leaf_id)
             e_det = float(run.errors(det, rbc.ERR_EACH)[0])
             entry = {"Q": Q, "deterministic": e_det}
             for var in variants:
                 mode = VARIANTS[var]
                 count = K if kind == "average" else trials
-                Cs = run.realize(run.plans(Q, mode, count, (seed << 32) + (Q << 24), scope), leaf_id)
+                base = (seed << 32) + (Q << 24)
+                Cs = run.realize(run.plan(Q, mode, scope), np.arange(base, base + count, dtype=np.uint64), leaf_id)
                 realizations += count
                 if kind == "average":
                     e = run.errors(Cs, rbc.ERR_AVERAGE)

@@ -99,8 +99,8 @@ SIGNATURES = {
                             C.c_size_t, _P]),
     "rbc_norms_work_size": (C.c_size_t, []),
     "rbc_realizations_workspace_size": (C.c_size_t, [_P, C.c_int64, C.c_int, C.c_int, C.c_int64]),
-    "rbc_matmul_realizations": (C.c_int, [C.POINTER(_P), C.c_int64, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64,
-                                          C.c_int64, C.c_int64, C.c_int, C.c_int, _P, C.c_size_t, _P]),
+    "rbc_matmul_realizations": (C.c_int, [_P, C.POINTER(C.c_uint64), C.c_int64, _P, _P, _P, C.c_int64, C.c_int64,
+                                          C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, _P, C.c_size_t, _P]),
     "rbc_realization_errors": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int64,
                                          C.c_int, _P, _P, C.c_size_t, _P]),
     "rbc_realization_errors_work_size": (C.c_size_t, [C.c_int64, C.c_int64]),
@@ -257,12 +257,14 @@ def norms(X, Y=None, stream=None, work=None, out=None):
     return out
 
 
-def realizations(plans, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, stream=None, batch=None):
-    """K independent realizations through rbc_matmul_realizations: realization k uses plans[k];
-    returns (or fills) a K x N x N tensor.  `batch` bounds how many realizations share the
-    workspace at once (default: all)."""
+def realizations(plan: Plan, seeds, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, stream=None,
+                 batch=None):
+    """Independent realizations of `plan`'s product, realization k drawn from seeds[k]
+    (rbc_matmul_realizations); returns (or fills) a K x N x N tensor.  `batch` bounds how
+    many realizations share the workspace at once (default: all)."""
     import torch
-    K, N = len(plans), A.shape[0]
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(-1))
+    K, N = sd.size, A.shape[0]
     if A.shape != (N, N) or B.shape != (N, N) or A.stride(1) != 1 or B.stride(1) != 1:
         raise ValueError("square N x N inputs with unit column stride required")
     io = _io_of(A)
@@ -274,12 +276,12 @@ def realizations(plans, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, 
         raise ValueError("C_out must be K x N x N with unit column stride")
     if workspace is None:
         b = K if batch is None else max(1, min(K, batch))
-        need = int(lib().rbc_realizations_workspace_size(plans[0].handle, N, io, leaf, b))
+        need = int(lib().rbc_realizations_workspace_size(plan.handle, N, io, leaf, b))
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
-    handles = (_P * K)(*[p.handle.value for p in plans])
-    check(lib().rbc_matmul_realizations(handles, K, A.data_ptr(), B.data_ptr(), C_out.data_ptr(), N, A.stride(0),
-                                        B.stride(0), C_out.stride(1), C_out.stride(0), io, leaf,
-                                        workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)),
+    check(lib().rbc_matmul_realizations(plan.handle, sd.ctypes.data_as(C.POINTER(C.c_uint64)), K, A.data_ptr(),
+                                        B.data_ptr(), C_out.data_ptr(), N, A.stride(0), B.stride(0),
+                                        C_out.stride(1), C_out.stride(0), io, leaf, workspace.data_ptr(),
+                                        workspace.numel(), _stream_ptr(stream)),
           "rbc_matmul_realizations")
     return C_out
 

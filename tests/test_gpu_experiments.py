@@ -9,6 +9,8 @@
   * unbiasedness seen through the harness: the error of the average of K realizations of a
     perturbed Strassen formula (Section 3.1) falls like the per-realization spread / sqrt(K)
     (Props. 3 and 6), while the deterministic recursion keeps its error."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -51,19 +53,22 @@ def test_batch_equals_single_calls(rbc, case, io):
     leaf = rbc.LEAF_F64 if io == "f64" else rbc.LEAF_F32
     sc = rbc.DRAW_PER_LEVEL if scope == "level" else rbc.DRAW_PER_NODE
     K = 7
-    plans = [rbc.Plan(U, V, W, levels=L, seed=100 + k, rand_mode=MODES[mode], draw_scope=sc) for k in range(K)]
+    seeds = [100 + k for k in range(K)]
+    plan = rbc.Plan(U, V, W, levels=L, seed=seeds[3], rand_mode=MODES[mode], draw_scope=sc)
     _, _, A, B = _inputs(N, 11, dt)
     ioc = rbc.IO_F64 if io == "f64" else rbc.IO_F32
     # a workspace for 3 realizations: batches of 3, 3, 1
-    need3 = int(rbc.lib().rbc_realizations_workspace_size(plans[0].handle, N, ioc, leaf, 3))
+    need3 = int(rbc.lib().rbc_realizations_workspace_size(plan.handle, N, ioc, leaf, 3))
     ws = torch.empty(need3, dtype=torch.uint8, device="cuda")
     Cs = torch.full((K, N, N), float("nan"), dtype=dt, device="cuda")
-    rbc.realizations(plans, A, B, Cs, leaf=leaf, workspace=ws)
-    whole = rbc.realizations(plans, A, B, leaf=leaf)  # everything in one batch
+    rbc.realizations(plan, seeds, A, B, Cs, leaf=leaf, workspace=ws)
+    whole = rbc.realizations(plan, seeds, A, B, leaf=leaf)  # everything in one batch
     torch.cuda.synchronize()
     assert torch.equal(Cs, whole)
     for k in (0, 3, 6):
-        one = rbc.matmul(plans[k], A, B, leaf=leaf, decode=2)
+        # a plan created with seed k computes realization k alone
+        pk = rbc.Plan(U, V, W, levels=L, seed=seeds[k], rand_mode=MODES[mode], draw_scope=sc)
+        one = rbc.matmul(pk, A, B, leaf=leaf, decode=2)
         torch.cuda.synchronize()
         assert torch.equal(Cs[k], one), k
     if L > 0 and mode != "none":
@@ -74,15 +79,15 @@ def test_batch_equals_single_calls(rbc, case, io):
 def test_batch_equals_single_calls_tensor_core_leaves(rbc, leaf):
     U, V, W = formula("laderman")
     N, L, K = 9 * 24, 2, 5
-    plans = [rbc.Plan(U, V, W, levels=L, seed=7 + k) for k in range(K)]
+    plan = rbc.Plan(U, V, W, levels=L, seed=0)
     _, _, A, B = _inputs(N, 3, torch.float32)
     lf = rbc.LEAF_NAMES[leaf]
-    need2 = int(rbc.lib().rbc_realizations_workspace_size(plans[0].handle, N, rbc.IO_F32, lf, 2))
+    need2 = int(rbc.lib().rbc_realizations_workspace_size(plan.handle, N, rbc.IO_F32, lf, 2))
     ws = torch.empty(need2, dtype=torch.uint8, device="cuda")
-    Cs = rbc.realizations(plans, A, B, leaf=lf, workspace=ws)
+    Cs = rbc.realizations(plan, [7 + k for k in range(K)], A, B, leaf=lf, workspace=ws)
     torch.cuda.synchronize()
     for k in range(K):
-        one = rbc.matmul(plans[k], A, B, leaf=lf, decode=2)
+        one = rbc.matmul(rbc.Plan(U, V, W, levels=L, seed=7 + k), A, B, leaf=lf, decode=2)
         torch.cuda.synchronize()
         assert torch.equal(Cs[k], one), k
 
@@ -95,8 +100,8 @@ def test_realizations_match_the_oracle(rbc, io):
     leaf = rbc.LEAF_F64 if io == "f64" else rbc.LEAF_F32
     An, Bn, A, B = _inputs(N, 5, dt)
     for scope, osc in ((rbc.DRAW_PER_LEVEL, o.DRAW_PER_LEVEL), (rbc.DRAW_PER_NODE, o.DRAW_PER_NODE)):
-        plans = [rbc.Plan(U, V, W, levels=L, seed=40 + k, draw_scope=scope) for k in range(5)]
-        Cs = rbc.realizations(plans, A, B, leaf=leaf).double().cpu().numpy()
+        plan = rbc.Plan(U, V, W, levels=L, seed=0, draw_scope=scope)
+        Cs = rbc.realizations(plan, [40 + k for k in range(5)], A, B, leaf=leaf).double().cpu().numpy()
         if io == "f32":
             An32, Bn32 = A.double().cpu().numpy(), B.double().cpu().numpy()
         for k in range(5):
@@ -150,20 +155,18 @@ def test_batch_arguments(rbc):
     U, V, W = formula("strassen")
     _, _, A, B = _inputs(64, 1, torch.float64)
     p1 = rbc.Plan(U, V, W, levels=2, seed=1)
-    p2 = rbc.Plan(U, V, W, levels=1, seed=2)  # different depth
-    with pytest.raises(rbc.RbcError) as e:
-        rbc.realizations([p1, p2], A, B, leaf=rbc.LEAF_F64)
-    assert e.value.status == 1
-    p3 = rbc.Plan(U, V, W, levels=2, seed=2, rand_mode=rbc.RAND_SIGN)  # different mode
-    with pytest.raises(rbc.RbcError):
-        rbc.realizations([p1, p3], A, B, leaf=rbc.LEAF_F64)
     tiny = torch.empty(256, dtype=torch.uint8, device="cuda")
     with pytest.raises(rbc.RbcError) as e:
-        rbc.realizations([p1, p1], A, B, leaf=rbc.LEAF_F64, workspace=tiny)
+        rbc.realizations(p1, [1, 2], A, B, leaf=rbc.LEAF_F64, workspace=tiny)
     assert e.value.status == 2
+    Cs = torch.empty((2, 64, 64), dtype=torch.float64, device="cuda")
+    st = rbc.lib().rbc_matmul_realizations(p1.handle, (ctypes.c_uint64 * 2)(1, 2), 2, A.data_ptr(), B.data_ptr(),
+                                           Cs.data_ptr(), 64, 64, 64, 64, 64 * 63, rbc.IO_F64, rbc.LEAF_F64,
+                                           tiny.data_ptr(), tiny.numel(), None)
+    assert st == 1  # strideC < ldc * N: the outputs would overlap
     # L = 0: K copies of the standard product
-    p0 = [rbc.Plan(U, V, W, levels=0, seed=k) for k in range(3)]
-    Cs = rbc.realizations(p0, A, B, leaf=rbc.LEAF_F64)
+    p0 = rbc.Plan(U, V, W, levels=0, seed=0)
+    Cs = rbc.realizations(p0, [0, 1, 2], A, B, leaf=rbc.LEAF_F64)
     torch.cuda.synchronize()
     assert torch.equal(Cs[0], Cs[2])
     np.testing.assert_allclose(Cs[1].cpu().numpy(), (A @ B).cpu().numpy(), rtol=0, atol=1e-11)
@@ -181,14 +184,14 @@ def test_harness_unbiasedness(rbc):
     np.testing.assert_allclose(run.ref.cpu().numpy(), A @ B, rtol=0, atol=1e-11)
     K = 2048
     for Q in (1, 2, 3):
-        Cs = run.realize(run.plans(Q, rbc.RAND_FULL, K, 7 << 20, rbc.DRAW_PER_LEVEL))
+        Cs = run.realize(run.plan(Q, rbc.RAND_FULL, rbc.DRAW_PER_LEVEL), np.arange(K) + (7 << 20))
         each = run.errors(Cs, rbc.ERR_EACH)
         avg = run.errors(Cs, rbc.ERR_AVERAGE)
         rms = float(np.sqrt(np.mean(each**2)))
         assert avg[0] == pytest.approx(each[0], rel=1e-12)
         # E ||avg_K - AB||^2 = E ||F - AB||^2 / K for an unbiased estimator
         assert 0.3 * rms / np.sqrt(K) <= avg[-1] <= 3.0 * rms / np.sqrt(K), (Q, avg[-1], rms)
-        det = run.realize(run.plans(Q, rbc.RAND_NONE, 2, 0, rbc.DRAW_PER_LEVEL))
+        det = run.realize(run.plan(Q, rbc.RAND_NONE, rbc.DRAW_PER_LEVEL), [0, 1])
         e_det = run.errors(det, rbc.ERR_AVERAGE)
         assert e_det[1] == pytest.approx(e_det[0], rel=1e-12)
         assert avg[-1] < 0.2 * e_det[0]
