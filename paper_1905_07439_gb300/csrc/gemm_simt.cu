@@ -125,6 +125,81 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+// Small leaves (mp < 32, even): every product exactly mp x mp x mp.  A CTA stages the S and
+// T operands of `nl` consecutive leaves (contiguous ranges of the leaf buffers) in shared
+// memory; each thread computes 2 x 2 output blocks, summing over k in order as the tiled
+// kernel does.  Modes 0 (store M) and 2 (store C, L = 0).
+constexpr int kSmallThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) simt_small_gemm_kernel(const SimtGemmArgs a, int nl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int mp = (int)a.mp, hb = mp / 2, units = hb * hb;
+  const int per = mp * mp;  // elements of one leaf operand (lds = ldt = mp)
+  T* sS = reinterpret_cast<T*>(smem_raw);
+  T* sT = sS + (size_t)nl * per;
+  const int64_t groups = (a.leaves + nl - 1) / nl;
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    const int64_t l0 = g * nl;
+    const int cnt = (int)(a.leaves - l0 < nl ? a.leaves - l0 : nl);
+    const T* S = static_cast<const T*>(a.S) + l0 * a.strideS;
+    const T* Tg = static_cast<const T*>(a.T) + l0 * a.strideT;
+    __syncthreads();  // the previous group's readers are done
+    for (int e = threadIdx.x; e < cnt * per; e += kSmallThreads) {
+      sS[e] = S[e];
+      sT[e] = Tg[e];
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < cnt * units; u += kSmallThreads) {
+      const int lf = u / units, rem = u - lf * units, bi = rem / hb, bj = rem - bi * hb;
+      const T* sr = sS + lf * per + 2 * bi * mp;
+      const T* tc = sT + lf * per + 2 * bj;
+      T c00 = (T)0, c01 = (T)0, c10 = (T)0, c11 = (T)0;
+      for (int k = 0; k < mp; ++k) {
+        const T s0 = sr[k], s1 = sr[mp + k], t0 = tc[k * mp], t1 = tc[k * mp + 1];
+        c00 = fma(s0, t0, c00);
+        c01 = fma(s0, t1, c01);
+        c10 = fma(s1, t0, c10);
+        c11 = fma(s1, t1, c11);
+      }
+      const int64_t r = 2 * bi, c = 2 * bj;
+      if (a.mode == 0) {
+        T* M = static_cast<T*>(a.out) + (l0 + lf) * a.strideO + r * a.ldo + c;
+        M[0] = c00;
+        M[1] = c01;
+        M[a.ldo] = c10;
+        M[a.ldo + 1] = c11;
+      } else {
+        T* C = static_cast<T*>(a.out) + r * a.ldo + c;
+        const bool r1 = r + 1 < a.m, c1 = c + 1 < a.m;
+        if (r < a.m && c < a.m) C[0] = c00;
+        if (r < a.m && c1) C[1] = c01;
+        if (r1 && c < a.m) C[a.ldo] = c10;
+        if (r1 && c1) C[a.ldo + 1] = c11;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_small(const SimtGemmArgs& a, cudaStream_t st) {
+  const int64_t per = a.mp * a.mp;
+  if (a.mp % 2 || a.mp >= 32 || a.K != a.mp || a.lds != a.mp || a.ldt != a.mp || a.strideS != per ||
+      a.strideT != per || a.mode == 1 || (a.mode == 0 && (a.ldo != a.mp || a.strideO < per)))
+    return cudaErrorInvalidValue;
+  const int units = (int)(a.mp / 2 * (a.mp / 2));
+  // about two output blocks per thread, within 48 KB of shared memory
+  int nl = (2 * kSmallThreads + units - 1) / units;
+  const int fit = (int)((48 * 1024) / (2 * per * sizeof(T)));
+  nl = nl < fit ? nl : fit;
+  if (nl < 1) nl = 1;
+  const int64_t groups = (a.leaves + nl - 1) / nl;
+  const int64_t grid = groups < 152 * 16 ? groups : 152 * 16;
+  const size_t smem = (size_t)2 * nl * per * sizeof(T);
+  simt_small_gemm_kernel<T><<<(unsigned)grid, kSmallThreads, smem, st>>>(a, nl);
+  return cudaGetLastError();
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_tile(const Tables<T>& t, const SimtGemmArgs& a, cudaStream_t st) {
   if (a.mp % BM || a.mp % BN || a.K % BK) return cudaErrorInvalidValue;
@@ -141,12 +216,20 @@ int simt_tile(int io, int64_t m) {
   return m >= 128 ? 64 : 32;
 }
 
+int64_t simt_small_pad(int io, int64_t m) {
+  const int64_t q = io == RBC_IO_F64 ? 2 : 4;  // rows of whole vectors for the pass kernels
+  const int64_t mp = (m + q - 1) / q * q;
+  return mp < 32 ? mp : 0;
+}
+
 cudaError_t launch_simt_gemm(const Tables<float>& t, const SimtGemmArgs& a, cudaStream_t st) {
+  if (a.mp < 32) return launch_small<float>(a, st);
   if (simt_tile(RBC_IO_F32, a.m) == 128) return launch_tile<float, 128, 128, 8, 8, 8>(t, a, st);
   return launch_tile<float, 32, 32, 8, 2, 2>(t, a, st);
 }
 
 cudaError_t launch_simt_gemm(const Tables<double>& t, const SimtGemmArgs& a, cudaStream_t st) {
+  if (a.mp < 32) return launch_small<double>(a, st);
   if (simt_tile(RBC_IO_F64, a.m) == 64) return launch_tile<double, 64, 64, 8, 4, 4>(t, a, st);
   return launch_tile<double, 32, 32, 8, 2, 2>(t, a, st);
 }

@@ -204,8 +204,10 @@ struct EncodeEmitV {
   }
 };
 
-// Grid: x over row segments of kThreadsX * VEC positions, y over rows, z over parents.
-// Positions at or beyond nb (padding up to cols_out / rows_out) encode zeros.
+// Grid: x over the positions of the output blocks taken row after row (rows of cols_out
+// rounded up to VEC, so that a thread's VEC positions share a row), z over parents.  Small
+// blocks thus fill whole CTAs.  Positions at or beyond nb (padding up to cols_out /
+// rows_out) encode zeros.
 // FAST: every access of the launch is aligned and complete (nb and the output width are
 // multiples of VEC), so loads and stores are plain vectors without per-element checks.
 template <typename Tin, typename Tc, int N0, int G, int S, int VEC, bool FAST>
@@ -215,9 +217,10 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
   using Tout = typename StoreType<S>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tc* coef = reinterpret_cast<Tc*>(smem_raw);
-  const int64_t x = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
-  const int64_t y = blockIdx.y;
-  const bool inside = x < a.cols_out;
+  const int64_t colsv = (a.cols_out + VEC - 1) / VEC * VEC;
+  const int64_t pos = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
+  const int64_t y = pos / colsv, x = pos - y * colsv;
+  const bool inside = y < a.rows_out && x < a.cols_out;
   const int64_t outs = a.outs_per_parent;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();  // the previous parent's readers are done with the tables
@@ -423,8 +426,9 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
   constexpr int W = cpow(N0, G);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tc* coef = reinterpret_cast<Tc*>(smem_raw);
-  const int64_t x = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
-  const int64_t y = blockIdx.y;
+  const int64_t colsv = (a.nb + VEC - 1) / VEC * VEC;
+  const int64_t pos = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
+  const int64_t y = pos / colsv, x = pos - y * colsv;
   const bool valid = x < a.nb && y < a.nb;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();
@@ -456,7 +460,8 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
 inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
   const int64_t span = (int64_t)kThreadsX * vec;
-  return dim3((unsigned)((cols + span - 1) / span), (unsigned)rows, (unsigned)gz);
+  const int64_t positions = rows * ((cols + vec - 1) / vec * vec);
+  return dim3((unsigned)((positions + span - 1) / span), 1, (unsigned)gz);
 }
 
 template <typename K>
@@ -561,9 +566,9 @@ cudaError_t dec_n0(const Tables<Tc>& t, const PassArgs& a, int n0, int g, cudaSt
 template <typename Tin, int S>
 __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) {
   using Tout = typename StoreType<S>::T;
-  const int64_t x = (int64_t)blockIdx.x * kThreadsX + threadIdx.x;
-  const int64_t y = blockIdx.y;
-  if (x >= a.cols_out) return;
+  const int64_t pos = (int64_t)blockIdx.x * kThreadsX + threadIdx.x;  // row after row
+  const int64_t y = pos / a.cols_out, x = pos - y * a.cols_out;
+  if (y >= a.rows_out) return;
   const Tin* X = static_cast<const Tin*>(a.X);
   const int64_t sy = a.trans ? x : y, sx = a.trans ? y : x;  // source entry
   const double v = (sy < a.nb && sx < a.nb) ? (double)X[sy * a.ldx + sx] : 0.0;

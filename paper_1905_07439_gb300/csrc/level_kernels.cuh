@@ -66,6 +66,8 @@ struct SimtGemmArgs {
 };
 
 int simt_tile(int io, int64_t m);  // padding granularity of the SIMT leaf path
+// Padded size of a small leaf (exact-size product kernel), or 0 when m needs the tiled path.
+int64_t simt_small_pad(int io, int64_t m);
 cudaError_t launch_simt_gemm(const Tables<double>& t, const SimtGemmArgs& a, cudaStream_t st);
 cudaError_t launch_simt_gemm(const Tables<float>& t, const SimtGemmArgs& a, cudaStream_t st);
 

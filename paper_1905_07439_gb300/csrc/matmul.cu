@@ -86,8 +86,13 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   lo->store = leaf_store(leaf);
   lo->es_leaf = store_bytes(lo->store);
   lo->split = (leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32) ? 1 : 0;
+  // Small SIMT leaves take the exact-size product kernel, which stores M (staged decode) or
+  // C (L = 0); an explicitly fused decode keeps the tiled kernel.
+  const int64_t small = is_tc_leaf(leaf) || (decode_req == 1 && L > 0) ? 0 : simt_small_pad(io, lo->m);
   if (is_tc_leaf(leaf)) {
     lo->mp = tc_pad(lo->m);
+  } else if (small) {
+    lo->mp = small;
   } else {
     const int tile = simt_tile(io, lo->m);
     lo->mp = (lo->m + tile - 1) / tile * tile;
@@ -100,7 +105,8 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     // Fused scatter costs one read-modify-write of C per contribution; it pays only when C
     // stays in L2 and few leaves feed each element.
     const double c_bytes = (double)N * N * lo->es_io;
-    lo->decode = (fused_ok && L <= 1 && c_bytes <= 64.0 * (1 << 20) && fused_contributions(p) <= 4.0) ? 1 : 2;
+    lo->decode = (fused_ok && !small && L <= 1 && c_bytes <= 64.0 * (1 << 20) && fused_contributions(p) <= 4.0)
+                     ? 1 : 2;
   } else {
     lo->decode = decode_req;
   }

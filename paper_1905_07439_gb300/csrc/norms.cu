@@ -119,12 +119,44 @@ __global__ void __launch_bounds__(kErrThreads)
   }
 }
 
+// Error of the running average, in segments of `seg` realizations so that the sequential
+// scan over K runs in parallel: (1) per element, the sum of each segment; (2) per element,
+// the exclusive prefix of the segment sums, in segment order; (3) per segment, the running
+// sums continued from the prefix, one squared-error partial per realization and CTA.
+template <typename TC>
+__global__ void __launch_bounds__(kErrThreads)
+    err_segsum_kernel(const TC* C, int64_t K, int64_t N, int64_t ldc, int64_t strideC, int64_t seg, double* segsum) {
+  const int64_t total = N * N, base = (int64_t)blockIdx.x * kErrPer + threadIdx.x;
+  const int64_t n0 = (int64_t)blockIdx.y * seg, n1 = n0 + seg < K ? n0 + seg : K;
+#pragma unroll
+  for (int v = 0; v < kErrEpt; ++v) {
+    const int64_t e = base + (int64_t)v * kErrThreads;
+    if (e >= total) continue;
+    const int64_t r = e / N, c = e - r * N;
+    double sum = 0.0;
+    for (int64_t n = n0; n < n1; ++n) sum += (double)C[n * strideC + r * ldc + c];
+    segsum[(int64_t)blockIdx.y * total + e] = sum;
+  }
+}
+
+__global__ void __launch_bounds__(kErrThreads) err_prefix_kernel(int64_t total, int64_t nseg, double* segsum) {
+  const int64_t e = (int64_t)blockIdx.x * kErrThreads + threadIdx.x;
+  if (e >= total) return;
+  double run = 0.0;
+  for (int64_t s = 0; s < nseg; ++s) {
+    const double t = segsum[s * total + e];
+    segsum[s * total + e] = run;
+    run += t;
+  }
+}
+
 template <typename TC>
 __global__ void __launch_bounds__(kErrThreads)
     err_average_kernel(const TC* C, int64_t K, int64_t N, int64_t ldc, int64_t strideC, const double* Ref,
-                       int64_t ldr, double* part, int64_t nblk) {
+                       int64_t ldr, int64_t seg, const double* prefix, double* part, int64_t nblk) {
   __shared__ double sm[2][kErrThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kErrPer + threadIdx.x, total = N * N;
+  const int64_t n0 = (int64_t)blockIdx.y * seg, n1 = n0 + seg < K ? n0 + seg : K;
   int64_t off[kErrEpt];
   double ref[kErrEpt], sum[kErrEpt];
   TC next[kErrEpt];
@@ -135,16 +167,16 @@ __global__ void __launch_bounds__(kErrThreads)
     const int64_t r = in ? e / N : 0, c = in ? e - r * N : 0;
     off[v] = in ? r * ldc + c : -1;
     ref[v] = in ? Ref[r * ldr + c] : 0.0;
-    sum[v] = 0.0;
-    next[v] = off[v] >= 0 && K > 0 ? C[off[v]] : (TC)0;
+    sum[v] = in ? prefix[(int64_t)blockIdx.y * total + e] : 0.0;
+    next[v] = (off[v] >= 0 && n0 < n1) ? C[n0 * strideC + off[v]] : (TC)0;
   }
-  for (int64_t n = 0; n < K; ++n) {
+  for (int64_t n = n0; n < n1; ++n) {
     TC cur[kErrEpt];
 #pragma unroll
     for (int v = 0; v < kErrEpt; ++v) {
       cur[v] = next[v];
       // prefetch realization n + 1 while this one is reduced
-      next[v] = (off[v] >= 0 && n + 1 < K) ? C[(n + 1) * strideC + off[v]] : (TC)0;
+      next[v] = (off[v] >= 0 && n + 1 < n1) ? C[(n + 1) * strideC + off[v]] : (TC)0;
     }
     const double inv = 1.0 / (double)(n + 1);
     double d2 = 0.0;
@@ -179,6 +211,14 @@ __global__ void __launch_bounds__(kErrThreads)
 }
 
 inline int64_t err_blocks(int64_t N) { return (N * N + kErrPer - 1) / kErrPer; }
+// Segments of the running-average scan: 32 realizations each, at most 2^25 segment sums.
+inline int64_t err_segments(int64_t K, int64_t N) {
+  const int64_t want = (K + 31) / 32, cap = (int64_t)1 << 25;
+  const int64_t fit = N * N > 0 ? cap / (N * N) : want;
+  int64_t n = want < fit ? want : fit;
+  if (n > 65535) n = 65535;  // grid y
+  return n < 1 ? 1 : n;
+}
 
 }  // namespace
 }  // namespace rbc
@@ -187,7 +227,8 @@ using namespace rbc;
 
 extern "C" size_t rbc_realization_errors_work_size(int64_t K, int64_t N) {
   if (K < 0 || N < 0) return 0;
-  return sizeof(double) * ((size_t)K * (size_t)err_blocks(N) + 2 * kNormBlocks);
+  return sizeof(double) * ((size_t)K * (size_t)err_blocks(N) + 2 * kNormBlocks +
+                            (size_t)err_segments(K, N) * (size_t)(N * N));
 }
 
 extern "C" rbc_status rbc_realization_errors(const void* C, int ct, int64_t K, int64_t N, int64_t ldc,
@@ -215,12 +256,23 @@ extern "C" rbc_status rbc_realization_errors(const void* C, int ct, int64_t K, i
       err_each_kernel<double><<<grid, kErrThreads, 0, st>>>(static_cast<const double*>(C), K, N, ldc, strideC,
                                                             Ref, ldr, part, nblk);
   } else {
-    if (ct == RBC_IO_F32)
-      err_average_kernel<float><<<(unsigned)nblk, kErrThreads, 0, st>>>(static_cast<const float*>(C), K, N, ldc,
-                                                                        strideC, Ref, ldr, part, nblk);
-    else
-      err_average_kernel<double><<<(unsigned)nblk, kErrThreads, 0, st>>>(static_cast<const double*>(C), K, N, ldc,
-                                                                         strideC, Ref, ldr, part, nblk);
+    const int64_t nseg = err_segments(K, N), seg = (K + nseg - 1) / nseg;
+    double* segsum = ref_part + 2 * kNormBlocks;
+    const dim3 grid((unsigned)nblk, (unsigned)nseg);
+    const unsigned pgrid = (unsigned)((N * N + kErrThreads - 1) / kErrThreads);
+    if (ct == RBC_IO_F32) {
+      const float* Cf = static_cast<const float*>(C);
+      err_segsum_kernel<float><<<grid, kErrThreads, 0, st>>>(Cf, K, N, ldc, strideC, seg, segsum);
+      err_prefix_kernel<<<pgrid, kErrThreads, 0, st>>>(N * N, nseg, segsum);
+      err_average_kernel<float><<<grid, kErrThreads, 0, st>>>(Cf, K, N, ldc, strideC, Ref, ldr, seg, segsum, part,
+                                                              nblk);
+    } else {
+      const double* Cd = static_cast<const double*>(C);
+      err_segsum_kernel<double><<<grid, kErrThreads, 0, st>>>(Cd, K, N, ldc, strideC, seg, segsum);
+      err_prefix_kernel<<<pgrid, kErrThreads, 0, st>>>(N * N, nseg, segsum);
+      err_average_kernel<double><<<grid, kErrThreads, 0, st>>>(Cd, K, N, ldc, strideC, Ref, ldr, seg, segsum, part,
+                                                               nblk);
+    }
   }
   err_final_kernel<<<1, kErrThreads, 0, st>>>(part, K, nblk, ref_part, kNormBlocks, err);
   const cudaError_t e = cudaGetLastError();

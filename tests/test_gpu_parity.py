@@ -52,6 +52,14 @@ CASES_F64 = [
     ("noisy-strassen", 1, 2 * 130, o.RAND_FULL, o.DRAW_PER_NODE),
     ("noisy-strassen", 3, 8 * 17, o.RAND_FULL, o.DRAW_PER_LEVEL),
     ("noisy-laderman", 2, 9 * 11, o.RAND_FULL, o.DRAW_PER_NODE),
+    # small leaves (exact-size product kernel unless the decode is fused): L = 0 direct
+    # store, odd sizes, the largest small size and the first tiled one
+    ("strassen", 0, 20, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("laderman", 0, 31, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("laderman", 1, 3 * 3, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("strassen", 1, 2 * 29, o.RAND_FULL, o.DRAW_PER_NODE),
+    ("strassen", 1, 2 * 30, o.RAND_FULL, o.DRAW_PER_LEVEL),
+    ("strassen", 1, 2 * 31, o.RAND_FULL, o.DRAW_PER_NODE),
 ]
 
 
@@ -80,6 +88,10 @@ CASES_F32 = [
     ("strassen", 3, 8 * 45, "normal"),
     ("laderman", 2, 9 * 100, "normal"),
     ("noisy-strassen", 2, 4 * 260, "normal"),
+    ("strassen", 3, 8 * 10, "normal"),     # small leaves
+    ("laderman", 1, 3 * 7, "hard"),
+    ("strassen", 0, 26, "normal"),
+    ("strassen", 1, 2 * 27, "normal"),
 ]
 
 
