@@ -85,11 +85,16 @@ __host__ __device__ inline int subtree_nodes(int R, int G) {
   }
   return s;
 }
+// Coefficient rows of one child (n0^2 entries) padded to a multiple of 4 entries, so that a
+// row loads as 16-byte vectors.
+__host__ __device__ constexpr int coef_stride(int n0) { return (n0 * n0 + 3) / 4 * 4; }
+
 // Local id of the node at relative depth j with path prefix q: sum_{i<j} R^i + q.
 __device__ __forceinline__ int local_id(int R, int j, int q) { return subtree_nodes(R, j) + q; }
 
 // Expand the tables of the G-level subtree under launch parent p (at depth a.depth) into
-// coef[(local * R + r) * n0^2 + a * n0 + b] for tensor `which` (0 u^, 1 v^, 2 w^).
+// coef[(local * R + r) * coef_stride(n0) + a * n0 + b] for tensor `which` (0 u^, 1 v^, 2 w^);
+// the row padding holds zeros.
 template <typename Tc>
 __device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, int which, int64_t p,
                                Tc* coef) {
@@ -99,17 +104,21 @@ __device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, in
     hp = a.node_first + (p - real * a.real_parents);
   }
   const uint64_t* draws = t.draw + real * a.real_draws;
-  const int R = t.R, n0 = t.n0, nn = n0 * n0;
-  const int total = subtree_nodes(R, G) * R * nn;
+  const int R = t.R, n0 = t.n0, nn = n0 * n0, ns = coef_stride(n0);
+  const int total = subtree_nodes(R, G) * R * ns;
   const Tc* base = which == 0 ? t.U : (which == 1 ? t.V : t.W);
   const int cr = which == 1 ? 1 : 0;  // row stream: pi1/s1 (u^, w^) or pi2/s2 (v^)
   const int cc = which == 0 ? 1 : 2;  // column stream: pi2/s2 (u^) or pi3/s3 (v^, w^)
   const Tc sc = which == 2 ? t.scale : (Tc)1;
   const int nthreads = blockDim.x * blockDim.y;
   for (int e = threadIdx.y * blockDim.x + threadIdx.x; e < total; e += nthreads) {
-    const int local = e / (R * nn);
-    const int rem = e - local * R * nn;
-    const int r = rem / nn, ab = rem - r * nn, ra = ab / n0, cb = ab - ra * n0;
+    const int local = e / (R * ns);
+    const int rem = e - local * R * ns;
+    const int r = rem / ns, ab = rem - r * ns, ra = ab / n0, cb = ab - ra * n0;
+    if (ab >= nn) {
+      coef[e] = (Tc)0;
+      continue;
+    }
     int j = 0, start = 0, width = 1;
     while (local >= start + width) {
       start += width;
@@ -125,6 +134,32 @@ __device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, in
   }
 }
 
+// One child's coefficient row from shared memory, as 16-byte vectors.
+template <typename Tc, int N0>
+__device__ __forceinline__ void load_coefs(Tc (&c)[coef_stride(N0)], const Tc* src) {
+  constexpr int NS = coef_stride(N0);
+  if constexpr (sizeof(Tc) == 4) {
+#pragma unroll
+    for (int i = 0; i < NS / 4; ++i) {
+      const float4 v = reinterpret_cast<const float4*>(src)[i];
+      memcpy(&c[4 * i], &v, 16);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NS / 2; ++i) {
+      const double2 v = reinterpret_cast<const double2*>(src)[i];
+      memcpy(&c[2 * i], &v, 16);
+    }
+  }
+}
+
+// Zero coefficients are skipped in fp64 (its FMA pipe is the scarce resource); fp32 passes
+// run the dense, branch-free form, which measured faster.
+template <typename Tc>
+__device__ __forceinline__ bool use_coef(Tc c) {
+  return sizeof(Tc) == 4 || c != (Tc)0;
+}
+
 // ------------------------------------------------------------------ encode walk
 template <typename Tc, int N0, int G, int VEC>
 struct EncodeWalk {
@@ -132,9 +167,11 @@ struct EncodeWalk {
   template <class Emit>
   __device__ __forceinline__ static void go(const Tc* coef, int R, int j, int q, int64_t path,
                                             const Tc (&in)[W * W][VEC], Emit& emit) {
-    const Tc* row = coef + (size_t)local_id(R, j, q) * R * (N0 * N0);
+    constexpr int NS = coef_stride(N0);
+    const Tc* row = coef + (size_t)local_id(R, j, q) * R * NS;
     for (int r = 0; r < R; ++r) {
-      const Tc* c = row + r * (N0 * N0);
+      Tc c[NS];
+      load_coefs<Tc, N0>(c, row + r * NS);
       Tc cin[WC * WC][VEC];
 #pragma unroll
       for (int e = 0; e < WC * WC; ++e)
@@ -145,7 +182,7 @@ struct EncodeWalk {
 #pragma unroll
         for (int l = 0; l < N0; ++l) {
           const Tc cf = c[k * N0 + l];
-          if (cf != (Tc)0) {
+          if (use_coef(cf)) {
 #pragma unroll
             for (int u = 0; u < WC; ++u)
 #pragma unroll
@@ -182,6 +219,19 @@ __device__ __forceinline__ void store_some(T* dst, const T (&x)[VEC], bool vec, 
   }
 }
 
+// Two fp32 values rounded to a 16-bit leaf format (nearest even) with one instruction, and back.
+template <int S> struct Pair2;
+template <> struct Pair2<kStoreBF16> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ T cvt(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  static __device__ __forceinline__ float2 back(T v) { return __bfloat1622float2(v); }
+};
+template <> struct Pair2<kStoreF16> {
+  using T = __half2;
+  static __device__ __forceinline__ T cvt(float a, float b) { return __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ float2 back(T v) { return __half22float2(v); }
+};
+
 template <typename Tc, int S, int VEC>
 struct EncodeEmitV {
   using Tout = typename StoreType<S>::T;
@@ -191,6 +241,27 @@ struct EncodeEmitV {
   bool vec;
   __device__ __forceinline__ void operator()(int64_t path, const Tc (&val)[VEC]) {
     Tout* dst = Y + path * strideY + off;
+    if constexpr ((S == kStoreBF16 || S == kStoreF16) && sizeof(Tc) == 4 && VEC % 2 == 0) {
+      using P = Pair2<S>;
+      typename P::T h2[VEC / 2];
+      Tout hi[VEC];
+#pragma unroll
+      for (int i = 0; i < VEC / 2; ++i) h2[i] = P::cvt(val[2 * i], val[2 * i + 1]);
+      memcpy(hi, h2, sizeof(hi));
+      store_some<Tout, VEC>(dst, hi, vec, avail);
+      if (split) {
+        typename P::T l2[VEC / 2];
+        Tout lo[VEC];
+#pragma unroll
+        for (int i = 0; i < VEC / 2; ++i) {
+          const float2 h = P::back(h2[i]);
+          l2[i] = P::cvt(val[2 * i] - h.x, val[2 * i + 1] - h.y);
+        }
+        memcpy(lo, l2, sizeof(lo));
+        store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
+      }
+      return;
+    }
     Tout hi[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) hi[v] = to_store<S>((double)val[v]);
@@ -336,7 +407,8 @@ struct DecodeWalk {
   template <class Fetch>
   __device__ __forceinline__ static void go(const Tc* coef, int R, int j, int q, int64_t path,
                                             Tc (&out)[W * W][VEC], Fetch& fetch) {
-    const Tc* row = coef + (size_t)local_id(R, j, q) * R * (N0 * N0);
+    constexpr int NS = coef_stride(N0);
+    const Tc* row = coef + (size_t)local_id(R, j, q) * R * NS;
 #pragma unroll
     for (int e = 0; e < W * W; ++e)
 #pragma unroll
@@ -344,13 +416,14 @@ struct DecodeWalk {
     for (int r = 0; r < R; ++r) {
       Tc cout[WC * WC][VEC];
       DecodeWalk<Tc, N0, G - 1, VEC>::go(coef, R, j + 1, q * R + r, path * R + r, cout, fetch);
-      const Tc* c = row + r * (N0 * N0);
+      Tc c[NS];
+      load_coefs<Tc, N0>(c, row + r * NS);
 #pragma unroll
       for (int i = 0; i < N0; ++i)
 #pragma unroll
         for (int jj = 0; jj < N0; ++jj) {
           const Tc wv = c[i * N0 + jj];
-          if (wv != (Tc)0) {
+          if (use_coef(wv)) {
 #pragma unroll
             for (int u = 0; u < WC; ++u)
 #pragma unroll
@@ -372,7 +445,8 @@ struct DecodeWalk<Tc, N0, 1, VEC> {
   template <class Fetch>
   __device__ __forceinline__ static void go(const Tc* coef, int R, int j, int q, int64_t path,
                                             Tc (&out)[W * W][VEC], Fetch& fetch) {
-    const Tc* row = coef + (size_t)local_id(R, j, q) * R * (N0 * N0);
+    constexpr int NS = coef_stride(N0);
+    const Tc* row = coef + (size_t)local_id(R, j, q) * R * NS;
 #pragma unroll
     for (int e = 0; e < W * W; ++e)
 #pragma unroll
@@ -386,11 +460,12 @@ struct DecodeWalk<Tc, N0, 1, VEC> {
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         if (r0 + b < R) {
-          const Tc* c = row + (r0 + b) * (N0 * N0);
+          Tc c[NS];
+          load_coefs<Tc, N0>(c, row + (r0 + b) * NS);
 #pragma unroll
           for (int e = 0; e < N0 * N0; ++e) {
             const Tc wv = c[e];
-            if (wv != (Tc)0) {
+            if (use_coef(wv)) {
 #pragma unroll
               for (int v = 0; v < VEC; ++v) out[e][v] = out[e][v] + wv * m[b][v];
             }
@@ -475,7 +550,7 @@ inline bool aligned(const void* p, size_t bytes) { return ((uintptr_t)p % bytes)
 template <typename Tin, typename Tc, int S, int N0, int G>
 cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) {
   using Tout = typename StoreType<S>::T;
-  const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
+  const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * coef_stride(N0) * sizeof(Tc);
   if (a_in.trans) {
     if (a_in.rows_out % 8 || a_in.cols_out % 32 || a_in.rows_out != a_in.cols_out) return cudaErrorInvalidValue;
     const int64_t gz = a_in.parents < 65535 ? a_in.parents : 65535;
@@ -525,7 +600,7 @@ cudaError_t enc_n0(const Tables<Tc>& t, const PassArgs& a, int n0, int g, cudaSt
 template <typename Tm, typename To, typename Tc, int N0, int G>
 cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) {
   constexpr int VEC = Vec<Tc, N0, G>::value;
-  const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * N0 * N0 * sizeof(Tc);
+  const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * coef_stride(N0) * sizeof(Tc);
   PassArgs a = a_in;
   a.vload = a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tm));
   a.vstore = a.nb % VEC == 0 && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
@@ -586,7 +661,6 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 // intermediate.
 int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
 
-size_t pass_smem_bytes(int R, int n0, int g, int es) { return (size_t)subtree_nodes(R, g) * R * n0 * n0 * es; }
 
 cudaError_t launch_encode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, int io, int store,
                                cudaStream_t st) {
