@@ -125,16 +125,18 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
-// Small leaves (mp < 32, even): every product exactly mp x mp x mp.  A CTA stages the S and
-// T operands of `nl` consecutive leaves (contiguous ranges of the leaf buffers) in shared
-// memory; each thread computes 2 x 2 output blocks, summing over k in order as the tiled
-// kernel does.  Modes 0 (store M) and 2 (store C, L = 0).
+// Small leaves (mp < 32, a multiple of 4): every product exactly m x m x m (the padding of
+// S and T is zero and is skipped).  A CTA stages the S and T operands of `nl` consecutive
+// leaves (contiguous ranges of the leaf buffers) in shared memory; each thread computes 2 x 2
+// output blocks of the first 2 ceil(m/2) rows and columns, summing over k in order as the
+// tiled kernel does.  Modes 0 (store M; rows and columns past those are left unwritten and
+// are never read) and 2 (store C, L = 0).
 constexpr int kSmallThreads = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads) simt_small_gemm_kernel(const SimtGemmArgs a, int nl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int mp = (int)a.mp, hb = mp / 2, units = hb * hb;
+  const int mp = (int)a.mp, mv = (int)a.m, hb = (mv + 1) / 2, units = hb * hb;
   const int per = mp * mp;  // elements of one leaf operand (lds = ldt = mp)
   T* sS = reinterpret_cast<T*>(smem_raw);
   T* sT = sS + (size_t)nl * per;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kSmallThreads) simt_small_gemm_kernel(const Si
       const T* sr = sS + lf * per + 2 * bi * mp;
       const T* tc = sT + lf * per + 2 * bj;
       T c00 = (T)0, c01 = (T)0, c10 = (T)0, c11 = (T)0;
-      for (int k = 0; k < mp; ++k) {
+      for (int k = 0; k < mv; ++k) {
         const T s0 = sr[k], s1 = sr[mp + k], t0 = tc[k * mp], t1 = tc[k * mp + 1];
         c00 = fma(s0, t0, c00);
         c01 = fma(s0, t1, c01);
@@ -184,10 +186,10 @@ __global__ void __launch_bounds__(kSmallThreads) simt_small_gemm_kernel(const Si
 template <typename T>
 cudaError_t launch_small(const SimtGemmArgs& a, cudaStream_t st) {
   const int64_t per = a.mp * a.mp;
-  if (a.mp % 2 || a.mp >= 32 || a.K != a.mp || a.lds != a.mp || a.ldt != a.mp || a.strideS != per ||
+  if (a.mp % 4 || a.mp >= 32 || a.m > a.mp || a.K != a.mp || a.lds != a.mp || a.ldt != a.mp || a.strideS != per ||
       a.strideT != per || a.mode == 1 || (a.mode == 0 && (a.ldo != a.mp || a.strideO < per)))
     return cudaErrorInvalidValue;
-  const int units = (int)(a.mp / 2 * (a.mp / 2));
+  const int units = (int)((a.m + 1) / 2 * ((a.m + 1) / 2));
   // about two output blocks per thread, within 48 KB of shared memory
   int nl = (2 * kSmallThreads + units - 1) / units;
   const int fit = (int)((48 * 1024) / (2 * per * sizeof(T)));
@@ -217,8 +219,8 @@ int simt_tile(int io, int64_t m) {
 }
 
 int64_t simt_small_pad(int io, int64_t m) {
-  const int64_t q = io == RBC_IO_F64 ? 2 : 4;  // rows of whole vectors for the pass kernels
-  const int64_t mp = (m + q - 1) / q * q;
+  (void)io;
+  const int64_t mp = (m + 3) / 4 * 4;  // rows of whole 16-byte vectors for the pass kernels
   return mp < 32 ? mp : 0;
 }
 

@@ -260,27 +260,33 @@ struct EncodeEmitV {
         memcpy(lo, l2, sizeof(lo));
         store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
       }
-      return;
-    }
-    Tout hi[VEC];
+    } else {
+      Tout hi[VEC];
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) hi[v] = to_store<S>((double)val[v]);
-    store_some<Tout, VEC>(dst, hi, vec, avail);
-    if (split) {
-      Tout lo[VEC];
+      for (int v = 0; v < VEC; ++v) hi[v] = to_store<S>((double)val[v]);
+      store_some<Tout, VEC>(dst, hi, vec, avail);
+      if (split) {
+        Tout lo[VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(val[v] - (Tc)from_store<S>(hi[v])));
-      store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
+        for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(val[v] - (Tc)from_store<S>(hi[v])));
+        store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
+      }
     }
   }
 };
 
-// Grid: x over the positions of the output blocks taken row after row (rows of cols_out
-// rounded up to VEC, so that a thread's VEC positions share a row), z over parents.  Small
-// blocks thus fill whole CTAs.  Positions at or beyond nb (padding up to cols_out /
-// rows_out) encode zeros.
-// FAST: every access of the launch is aligned and complete (nb and the output width are
-// multiples of VEC), so loads and stores are plain vectors without per-element checks.
+// Physical column x of a padded layout -> logical column (valid when x % seg < m).
+__device__ __forceinline__ int64_t logical_col(int64_t x, int64_t seg, int64_t m) {
+  const int64_t s = x / seg;
+  return s * m + (x - s * seg);
+}
+
+// Grid: x over the physical positions of the output blocks taken row after row (rows of
+// cols_out rounded up to VEC, so that a thread's VEC positions share a row and a column
+// segment), z over parents.  Small blocks thus fill whole CTAs.  Padding positions encode
+// zeros.
+// FAST: every access of the launch is aligned and complete (vector loads and stores, and
+// whole vectors of valid positions), so there are no per-element checks.
 template <typename Tin, typename Tc, int N0, int G, int S, int VEC, bool FAST>
 __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_constant__ Tables<Tc> t,
                                                                 const PassArgs a) {
@@ -293,6 +299,11 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
   const int64_t y = pos / colsv, x = pos - y * colsv;
   const bool inside = y < a.rows_out && x < a.cols_out;
   const int64_t outs = a.outs_per_parent;
+  const int64_t xs = x % a.seg;                      // position inside its column segment
+  const int64_t avail_in = a.mval - xs;              // valid positions from x on
+  // source column offset of this position inside a sub-block
+  const int64_t xsrc = a.plain ? logical_col(x, a.seg, a.mval) : x;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;   // sub-block column pitch in X
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();  // the previous parent's readers are done with the tables
     expand_subtree(t, a, G, a.tensor, p, coef);
@@ -306,7 +317,7 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
     emit.split = a.split;
     emit.vec = FAST || a.vstore != 0;
     emit.avail = FAST ? VEC : a.cols_out - x;
-    if (y >= a.nb || x >= a.nb) {  // padding only: zero outputs
+    if (y >= a.nb || avail_in <= 0) {  // padding only: zero outputs
       Tc z[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; ++v) z[v] = (Tc)0;
@@ -314,19 +325,19 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
       continue;
     }
     const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
-    const bool full = FAST || (a.vload && x + VEC <= a.nb);
+    const bool full = FAST || (a.vload && avail_in >= VEC);
     Tc in[W * W][VEC];
 #pragma unroll
     for (int k = 0; k < W; ++k)
 #pragma unroll
       for (int l = 0; l < W; ++l) {
-        const Tin* src = X + (k * a.nb + y) * a.ldx + l * a.nb + x;
+        const Tin* src = X + (k * a.nb + y) * a.ldx + l * colstep + xsrc;
         Tin raw[VEC];
         if (full) {
           load_vec<Tin, VEC>(raw, src);
         } else {
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) raw[v] = (x + v < a.nb) ? src[v] : (Tin)0;
+          for (int v = 0; v < VEC; ++v) raw[v] = (v < avail_in) ? src[v] : (Tin)0;
         }
 #pragma unroll
         for (int v = 0; v < VEC; ++v) in[k * W + l][v] = (Tc)raw[v];
@@ -371,7 +382,8 @@ __global__ void __launch_bounds__(256) encode_pass_trans_kernel(const __grid_con
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int64_t x0 = (int64_t)blockIdx.x * 32, y0 = (int64_t)blockIdx.y * 8;
   const int64_t x = x0 + tx, y = y0 + ty;
-  const bool valid = y < a.nb && x < a.nb;
+  const bool valid = y < a.nb && x < a.mval;  // the final pass: one segment per leaf row
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();
     expand_subtree(t, a, G, a.tensor, p, coef);
@@ -395,7 +407,7 @@ __global__ void __launch_bounds__(256) encode_pass_trans_kernel(const __grid_con
     for (int k = 0; k < W; ++k)
 #pragma unroll
       for (int l = 0; l < W; ++l)
-        in[k * W + l][0] = valid ? (Tc)X[(k * a.nb + y) * a.ldx + l * a.nb + x] : (Tc)0;
+        in[k * W + l][0] = valid ? (Tc)X[(k * a.nb + y) * a.ldx + l * colstep + x] : (Tc)0;
     EncodeWalk<Tc, N0, G, 1>::go(coef, t.R, 0, 0, 0, in, emit);
   }
 }
@@ -501,10 +513,16 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
   constexpr int W = cpow(N0, G);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tc* coef = reinterpret_cast<Tc*>(smem_raw);
-  const int64_t colsv = (a.nb + VEC - 1) / VEC * VEC;
+  const int64_t colsv = (a.xcol + VEC - 1) / VEC * VEC;  // physical width of a child
   const int64_t pos = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
   const int64_t y = pos / colsv, x = pos - y * colsv;
-  const bool valid = x < a.nb && y < a.nb;
+  const int64_t xs = x % a.seg, avail = a.mval - xs;
+  const bool valid = y < a.nb && x < a.xcol && avail > 0;
+  // destination column inside a sub-block of the parent, and the sub-block column pitch
+  const int64_t xdst = a.plain ? logical_col(x, a.seg, a.mval) : x;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  // recursive parents take whole vectors (padding lanes hold zeros and are never read)
+  const int64_t avail_st = FAST ? VEC : (a.plain ? avail : VEC);
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     __syncthreads();
     expand_subtree(t, a, G, 2, p, coef);
@@ -514,7 +532,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
     fetch.M = static_cast<const Tm*>(a.X) + p * a.outs_per_parent * a.strideX;
     fetch.strideM = a.strideX;
     fetch.off = y * a.ldx + x;
-    fetch.avail = FAST ? VEC : a.nb - x;
+    fetch.avail = FAST ? VEC : avail;
     fetch.vec = FAST || a.vload != 0;
     Tc out[W * W][VEC];
     DecodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, out, fetch);
@@ -527,7 +545,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
         To o[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] = (To)out[k * W + l][v];
-        store_some<To, VEC>(P + (k * a.nb + y) * a.ldy + l * a.nb + x, o, vs, FAST ? VEC : a.nb - x);
+        store_some<To, VEC>(P + (k * a.nb + y) * a.ldy + l * colstep + xdst, o, vs, avail_st);
       }
   }
 }
@@ -563,9 +581,12 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   }
   constexpr int VEC = Vec<Tc, N0, G>::value;
   PassArgs a = a_in;
-  a.vload = a.nb % VEC == 0 && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
+  if (a.seg <= 0 || a.seg % 4 || a.mval <= 0 || a.mval > a.seg) return cudaErrorInvalidValue;
+  // a plain input's columns are aligned when every segment starts aligned (or there is one)
+  const bool xalign = a.plain ? (a.nb % VEC == 0 && (a.mval % VEC == 0 || a.cols_out <= a.seg)) : a.xcol % VEC == 0;
+  a.vload = xalign && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
   a.vstore = a.ldy % VEC == 0 && a.strideY % VEC == 0 && a.kpanel % VEC == 0 && aligned(a.Y, VEC * sizeof(Tout));
-  const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0;
+  const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0 && a.mval % VEC == 0;
   auto kern = fast ? encode_pass_kernel<Tin, Tc, N0, G, S, VEC, true> : encode_pass_kernel<Tin, Tc, N0, G, S, VEC, false>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
@@ -602,13 +623,15 @@ cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   constexpr int VEC = Vec<Tc, N0, G>::value;
   const size_t smem = (size_t)subtree_nodes(t.R, G) * t.R * coef_stride(N0) * sizeof(Tc);
   PassArgs a = a_in;
+  if (a.seg <= 0 || a.seg % 4 || a.mval <= 0 || a.mval > a.seg || a.xcol % a.seg) return cudaErrorInvalidValue;
+  const bool yalign = a.plain ? (a.nb % VEC == 0 && (a.mval % VEC == 0 || a.xcol <= a.seg)) : true;
   a.vload = a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tm));
-  a.vstore = a.nb % VEC == 0 && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
-  const bool fast = a.vload && a.vstore && a.nb % VEC == 0;
+  a.vstore = yalign && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
+  const bool fast = a.vload && a.vstore && a.mval % VEC == 0;
   auto kern = fast ? decode_pass_kernel<Tm, To, Tc, N0, G, VEC, true> : decode_pass_kernel<Tm, To, Tc, N0, G, VEC, false>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<pass_grid(a.nb, a.nb, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
+  kern<<<pass_grid(a.nb, a.xcol, a.parents, VEC), kThreadsX, smem, st>>>(t, a);
   return cudaGetLastError();
 }
 

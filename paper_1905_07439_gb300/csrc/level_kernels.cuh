@@ -8,12 +8,25 @@
 namespace rbc {
 
 // One encode or decode pass over G consecutive levels (parents at depth `depth`).
+//
+// Column layouts.  A block of the recursion is nb_d x nb_d.  Plain layout: element (y, x) at
+// column x.  Recursive padded layout (the intermediates): every leaf-sized column segment of
+// m logical columns is stored in seg >= m physical columns (seg a multiple of 4), so every
+// sub-block, at every level, starts 16-byte aligned; a block with n0^k segments per row is
+// seg * n0^k physical columns wide and the sub-block column Lc of a grid starts at Lc times
+// the sub-block's physical width.  Physical column x holds logical column
+// (x / seg) * m + x % seg when x % seg < m (else padding, never read).
+//
 //   encode: X = parents (parent p at X + p*strideX, leading dim ldx), each an n0^G x n0^G grid
-//           of nb x nb blocks; Y = outputs, output `path` of parent p at
-//           Y + (p*outs_per_parent + path)*strideY, leading dim ldy, rows_out x cols_out written
-//           (entries beyond nb are zero padding), split panels [hi | lo] kpanel apart.
+//           of nb x nb blocks, plain (plain = 1) or recursive with sub-block width xcol;
+//           Y = outputs, output `path` of parent p at Y + (p*outs_per_parent + path)*strideY,
+//           leading dim ldy, rows_out x cols_out physical positions written (padding
+//           positions are zeros), split panels [hi | lo] kpanel apart.  Positions x with
+//           x % seg >= mval or rows y >= nb are padding.
 //   decode: X = children (child `path` of parent p at X + (p*outs_per_parent + path)*strideX,
-//           leading dim ldx, nb x nb valid); Y = parents (p*strideY, leading dim ldy).
+//           leading dim ldx), nb rows x xcol physical columns (padding as above); Y = parents
+//           (p*strideY, leading dim ldy), plain (plain = 1) or recursive with sub-block
+//           width xcol.
 // Draw set of a node at relative depth j with heap id n: draw[dbase[j] + n - dfirst[j]]
 // (per-node scope) or draw[depth + j] (per-level scope).
 // Realization batches: with real_parents > 0 the parents of the launch belong to consecutive
@@ -26,6 +39,9 @@ struct PassArgs {
   int64_t ldy, strideY;
   int64_t nb;
   int64_t rows_out, cols_out;
+  int64_t seg, mval;  // column segment pitch and its valid width (see above)
+  int64_t xcol;       // physical width of an nb x nb sub-block in the recursive layout
+  int plain;          // encode: X plain; decode: Y plain
   int64_t parents;
   int64_t outs_per_parent;
   int64_t node_first;

@@ -98,6 +98,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     lo->mp = (lo->m + tile - 1) / tile * tile;
   }
   lo->K = lo->mp * (lo->split ? 2 : 1);
+  lo->seg = seg_pitch(lo->m);
   lo->passes = plan_passes(L, n0);
   const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;
   if (decode_req == 1 && !fused_ok) return fail(RBC_EUNSUPPORTED, "fused decode needs <= 1024 draw sets");
@@ -114,8 +115,8 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   size_t off = kStatusBytes;  // device status word(s) first
   for (int i = 1; i < lo->passes.count; ++i) {
     const int d = lo->passes.top[i];
-    const int64_t nd = lo->m * ipow(n0, L - d);
-    const size_t bytes = align256((size_t)(reals * ipow(R, d)) * nd * pad_ld(nd) * lo->es_io);
+    const int64_t nd = lo->m * ipow(n0, L - d), wd = lo->seg * ipow(n0, L - d);
+    const size_t bytes = align256((size_t)(reals * ipow(R, d)) * nd * wd * lo->es_io);
     lo->encA[d] = off;
     off += bytes;
     lo->encB[d] = off;
@@ -132,9 +133,9 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     off += align256((size_t)leaves * lo->mp * lo->mp * lo->es_acc);
     for (int i = 1; i < lo->passes.count; ++i) {
       const int d = lo->passes.top[i];
-      const int64_t nd = lo->m * ipow(n0, L - d);
+      const int64_t nd = lo->m * ipow(n0, L - d), wd = lo->seg * ipow(n0, L - d);
       lo->dec[d] = off;
-      off += align256((size_t)(reals * ipow(R, d)) * nd * pad_ld(nd) * lo->es_acc);
+      off += align256((size_t)(reals * ipow(R, d)) * nd * wd * lo->es_acc);
     }
   }
   lo->total = off;
@@ -252,6 +253,9 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
     a.split = lo.split;
     a.kpanel = lo.mp;
     a.trans = tensor == 1 && lo.store == kStoreTF32;
+    a.seg = lo.mp;
+    a.mval = lo.m;
+    a.plain = 1;
     cudaError_t e = launch_encode_pass(tab, a, n0, 0, io, lo.store, st);
     ++g_launches;
     return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
@@ -260,21 +264,25 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
     const int d = lo.passes.top[i], g = lo.passes.g[i];
     const bool last = i + 1 == lo.passes.count;
     const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
+    const int64_t w_par = lo.seg * ipow(n0, L - d), w_nb = lo.seg * ipow(n0, L - d - g);  // physical widths
     const int64_t P = ipow(R, d), outs = ipow(R, g);
     rbc_status s = for_each_launch(rs, d, g, [&](int64_t k0, int64_t kc, int64_t c0, int64_t cnt) {
       PassArgs a{};
       rbc_status s2 = launch_tables(rs, d, g, k0, kc, c0, cnt, &a, tab);
       if (s2 != RBC_OK) return s2;
       const int64_t first = k0 * P + c0;  // first parent of the launch, realization-major
-      if (d == 0) {
+      if (d == 0) {  // the caller's matrix, plain layout
         a.X = X;
         a.ldx = ldx;
         a.strideX = 0;
+        a.plain = 1;
       } else {
-        a.X = ws + enc[d] + (size_t)first * n_par * pad_ld(n_par) * lo.es_io;
-        a.ldx = pad_ld(n_par);
-        a.strideX = n_par * pad_ld(n_par);
+        a.X = ws + enc[d] + (size_t)first * n_par * w_par * lo.es_io;
+        a.ldx = w_par;
+        a.strideX = n_par * w_par;
       }
+      a.xcol = w_nb;
+      a.mval = lo.m;
       if (last) {
         a.Y = leafbuf + (size_t)first * outs * lo.mp * lo.K * lo.es_leaf;
         a.ldy = lo.K;
@@ -283,14 +291,16 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
         a.cols_out = lo.mp;
         a.split = lo.split;
         a.kpanel = lo.mp;
+        a.seg = lo.mp;  // one segment per leaf row
         // tf32 tensor-core leaves take T K-major: write T^T
         a.trans = tensor == 1 && lo.store == kStoreTF32;
       } else {
-        a.Y = ws + enc[d + g] + (size_t)first * outs * nb * pad_ld(nb) * lo.es_io;
-        a.ldy = pad_ld(nb);
-        a.strideY = nb * pad_ld(nb);
+        a.Y = ws + enc[d + g] + (size_t)first * outs * nb * w_nb * lo.es_io;
+        a.ldy = w_nb;
+        a.strideY = nb * w_nb;
         a.rows_out = nb;
-        a.cols_out = nb;
+        a.cols_out = w_nb;
+        a.seg = lo.seg;
       }
       a.nb = nb;
       a.parents = kc * cnt;
@@ -316,29 +326,34 @@ rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc
     const int d = lo.passes.top[i], g = lo.passes.g[i];
     const bool bottom = i + 1 == lo.passes.count;
     const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
+    const int64_t w_par = lo.seg * ipow(n0, L - d), w_nb = lo.seg * ipow(n0, L - d - g);  // physical widths
     const int64_t P = ipow(R, d), outs = ipow(R, g);
     rbc_status s = for_each_launch(rs, d, g, [&](int64_t k0, int64_t kc, int64_t c0, int64_t cnt) {
       PassArgs a{};
       rbc_status s2 = launch_tables(rs, d, g, k0, kc, c0, cnt, &a, tab);
       if (s2 != RBC_OK) return s2;
       const int64_t first = k0 * P + c0;
-      if (bottom) {
+      if (bottom) {  // leaf products: rows of mp >= seg columns
         a.X = ws + lo.M + (size_t)first * outs * lo.mp * lo.mp * lo.es_acc;
         a.ldx = lo.mp;
         a.strideX = lo.mp * lo.mp;
       } else {
-        a.X = ws + lo.dec[d + g] + (size_t)first * outs * nb * pad_ld(nb) * lo.es_acc;
-        a.ldx = pad_ld(nb);
-        a.strideX = nb * pad_ld(nb);
+        a.X = ws + lo.dec[d + g] + (size_t)first * outs * nb * w_nb * lo.es_acc;
+        a.ldx = w_nb;
+        a.strideX = nb * w_nb;
       }
-      if (d == 0) {  // one parent per realization
+      a.xcol = w_nb;
+      a.seg = lo.seg;
+      a.mval = lo.m;
+      if (d == 0) {  // one parent per realization: the caller's C, plain layout
         a.Y = static_cast<char*>(C) + (size_t)k0 * rs.strideC * lo.es_io;
         a.ldy = ldc;
         a.strideY = rs.strideC;
+        a.plain = 1;
       } else {
-        a.Y = ws + lo.dec[d] + (size_t)first * n_par * pad_ld(n_par) * lo.es_acc;
-        a.ldy = pad_ld(n_par);
-        a.strideY = n_par * pad_ld(n_par);
+        a.Y = ws + lo.dec[d] + (size_t)first * n_par * w_par * lo.es_acc;
+        a.ldy = w_par;
+        a.strideY = n_par * w_par;
       }
       a.nb = nb;
       a.parents = kc * cnt;

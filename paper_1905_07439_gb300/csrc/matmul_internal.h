@@ -14,8 +14,9 @@ namespace detail {
 constexpr size_t kStatusBytes = 256;  // device status word(s) at the start of a workspace
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-// Leading dimension of an intermediate operand: rows start 16-byte aligned for vector access.
-inline int64_t pad_ld(int64_t n) { return (n + 3) / 4 * 4; }
+// Column segment pitch of the intermediates' recursive padded layout: the leaf width m
+// rounded up to 4 elements, so that every sub-block of every level starts 16-byte aligned.
+inline int64_t seg_pitch(int64_t m) { return (m + 3) / 4 * 4; }
 
 extern thread_local int64_t g_launches;
 
@@ -30,6 +31,7 @@ struct Passes {
 
 struct Layout {
   int64_t m = 0, mp = 0, K = 0;
+  int64_t seg = 0;  // seg_pitch(m): an intermediate block at depth d is m n0^(L-d) rows x seg n0^(L-d) columns
   int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 staged passes
   size_t es_io = 0, es_acc = 0, es_leaf = 0;
   Passes passes;
