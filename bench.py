@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--decode", type=int, default=0, help="0 auto, 1 fused, 2 staged")
     ap.add_argument("--no-errors", action="store_true", help="skip the error pass after the timing")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "experiments"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "experiments", "precision"],
                     help="sweep: the at-scale fp32 sweep (default); batch: 512 uneven instances in one "
                          "grouped leaf launch replayed from a CUDA graph")
     ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--precision-n", type=int, default=16384, help="matrix size of the precision workload")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--cap-gb", type=float, default=120.0, help="workspace admission cap of the queue")
@@ -317,6 +318,28 @@ def run_ours(args):
             nr = rbc.norms(x["C"], truths[n]).cpu().numpy()
             errors.append({"formula": nm, "n": n, "L": L, "rel_fro_vs_fp64_ab": float(np.sqrt(nr[0] / nr[1]))})
         torch.cuda.synchronize(dev)
+        del truths
+        # the hard case: Uniform[0,1] with rows of A and columns of B scaled by 10^U(-3,3)
+        from rbc_inputs.matrices import matrix_pair
+        hard = {}
+        for plan, (nm, n, L) in zip(plans, cases):
+            if n not in hard:
+                hard.clear()
+                torch.cuda.empty_cache()
+                Ah, Bh = matrix_pair("hard", n, 500 + n)
+                hA = torch.tensor(Ah, dtype=torch.float32, device=dev)
+                hB = torch.tensor(Bh, dtype=torch.float32, device=dev)
+                hard[n] = (hA, hB, rbc.matmul(one, hA.double(), hB.double(), leaf=rbc.LEAF_F64))
+                del Ah, Bh
+            hA, hB, ht = hard[n]
+            x = inputs[n]
+            rbc.matmul(plan, hA, hB, x["C"], leaf=leaf, workspace=ws, decode=args.decode)
+            nr = rbc.norms(x["C"], ht).cpu().numpy()
+            for e in errors:
+                if (e["formula"], e["n"], e["L"]) == (nm, n, L):
+                    e["rel_fro_vs_fp64_ab_hard"] = float(np.sqrt(nr[0] / nr[1]))
+        hard.clear()
+        torch.cuda.synchronize(dev)
 
     # Our own classical product (L = 0, same leaf mode) on the same inputs, for comparison.
     classical = {}
@@ -547,6 +570,103 @@ def run_batch(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+PRECISION_LEAVES = ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "f32"]
+
+
+def run_precision(args):
+    """Precision sweep: randomized Strassen N = 16384, L = 1..3, every leaf mode with fp32
+    encode/decode, plus the fp64 leaf mode (fp64 I/O), on N(0,1) and row/column-scaled inputs.
+    Each result's error is measured against the fp64 standard product (on the GPU) and, on
+    sampled entries, against the oracle's RBC with the same draws."""
+    import numpy as np
+    import torch
+
+    import paper_1905_07439_gb300 as rbc
+    from oracle import rbc_oracle as o
+    from rbc_inputs import formula_by_name
+    from rbc_inputs.matrices import matrix_pair
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, levels = args.precision_n, (1, 2, 3)
+    U, V, W = formula_by_name("strassen")
+    plans = {L: rbc.Plan(U, V, W, levels=L, seed=2024 + L) for L in levels}
+    one = rbc.Plan(U, V, W, levels=0)
+    rng = np.random.default_rng(77)
+    rows, cols = rng.integers(0, N, 48), rng.integers(0, N, 48)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    results, tot_flops, tot_ms = [], 0.0, 0.0
+    with ClockSampler(local) as clk:
+        for dist in ("normal", "hard"):
+            An, Bn = matrix_pair(dist, N, 31)
+            An = An.astype(np.float32).astype(np.float64)
+            Bn = Bn.astype(np.float32).astype(np.float64)
+            A64 = torch.tensor(An, device=dev)
+            B64 = torch.tensor(Bn, device=dev)
+            A, B = A64.float(), B64.float()
+            truth = rbc.matmul(one, A64, B64, leaf=rbc.LEAF_F64)
+            orc = {L: o.rbc_entries(An, Bn, o.Plan(U, V, W, levels=L, seed=2024 + L), rows, cols) for L in levels}
+            ri, ci = torch.as_tensor(rows, device=dev), torch.as_tensor(cols, device=dev)
+            truth_s = truth[ri, ci].cpu().numpy()
+            C = torch.empty((N, N), dtype=torch.float32, device=dev)
+            for leaf_name in PRECISION_LEAVES + ["f64"]:
+                for L in levels:
+                    leaf = rbc.LEAF_NAMES[leaf_name]
+                    f64 = leaf_name == "f64"
+                    X, Y = (A64, B64) if f64 else (A, B)
+                    Cx = torch.empty((N, N), dtype=torch.float64, device=dev) if f64 else C
+                    io = rbc.IO_F64 if f64 else rbc.IO_F32
+                    ws = torch.empty(plans[L].workspace_size(N, io, leaf), dtype=torch.uint8, device=dev)
+                    run = lambda: rbc.matmul(plans[L], X, Y, Cx, leaf=leaf, workspace=ws)
+                    reps = 1 if f64 else (2 if leaf_name == "f32" else 3)
+                    if dist == "normal":
+                        ms = timed(run, reps)
+                    else:
+                        run()
+                        ms = None
+                    nr = rbc.norms(Cx, truth).cpu().numpy()
+                    cs = Cx[ri, ci].double().cpu().numpy()
+                    row = {"dist": dist, "leaf": leaf_name, "L": L,
+                           "rel_fro_vs_fp64_ab": float(np.sqrt(nr[0] / nr[1])),
+                           "sampled_rel_vs_oracle_rbc": float(np.linalg.norm(cs - orc[L]) / np.linalg.norm(orc[L])),
+                           "sampled_rel_oracle_vs_ab": float(np.linalg.norm(orc[L] - truth_s) / np.linalg.norm(truth_s))}
+                    if ms is not None:
+                        row["ms"] = round(ms, 3)
+                        row["eff_tflops"] = round(2.0 * N**3 / ms / 1e9, 1)
+                        if not f64:
+                            tot_flops += 2.0 * N**3
+                            tot_ms += ms
+                    results.append(row)
+                    del ws
+            del A64, B64, A, B, truth, C
+            torch.cuda.empty_cache()
+    line = {
+        "metric": METRIC, "value": round(world * tot_flops / (tot_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": round(tot_ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 io; " + ", ".join(PRECISION_LEAVES) + " leaves; f64",
+        "data": "synthetic (seeded N(0,1); Uniform[0,1] with rows of A / columns of B scaled by 10^U(-3,3))",
+        "config": {"workload": f"rbc-precision: strassen n={N} L=1..3, leaf modes " + "/".join(PRECISION_LEAVES)
+                               + " (fp32 encode/decode) and fp64 leaves (fp64 I/O); value = sum 2n^3 / summed time "
+                               "over the fp32-I/O products on N(0,1)", "parallelism": f"replicas x{world}"},
+        "results": results, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
 
 
 # Section 3's two experiment shapes: (figure, formula, io, N, Q, realizations, inputs)
@@ -840,6 +960,8 @@ def main():
         run_batch(args)
     elif args.workload == "experiments":
         run_experiments(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
