@@ -550,6 +550,122 @@ __global__ void __launch_bounds__(kThreadsX) decode_pass_kernel(const __grid_con
   }
 }
 
+// ------------------------------------------------------------------ sparse one-level decode
+// One-level fp32 decode passes of formulas with n0 >= 3 (Laderman: 51 of 207 coefficients of
+// W are nonzero).  Each child's nonzero coefficients are listed once per parent, in (i, j)
+// order, and a thread's output accumulators sit in shared memory, where the lists index them.
+// Every output sums over the children in the same order as the dense walk, without its zero
+// terms, so the results are the same.  (The same scheme for the encode measured slower than
+// the dense register walk, which keeps the encode dense.)
+//
+// Shared memory: [coef: R x NS][count: R][pairs: R x NN (entry, coefficient bits)]
+//                [stage: NN x kThreadsX x VEC floats].
+struct SparseSmem {
+  size_t cnt, pairs, stage, total;
+  __host__ __device__ SparseSmem(int R, int n0, int vec) {
+    const int nn = n0 * n0, ns = coef_stride(n0);
+    cnt = (size_t)R * ns * sizeof(float);                       // a multiple of 16 (ns % 4 == 0)
+    pairs = cnt + ((size_t)R * sizeof(int) + 15) / 16 * 16;
+    stage = pairs + ((size_t)R * nn * sizeof(int2) + 15) / 16 * 16;
+    total = stage + (size_t)nn * kThreadsX * vec * sizeof(float);
+  }
+};
+
+// Count and list the nonzero coefficients of every child (one-level subtree: node 0).
+__device__ __forceinline__ void build_lists(const float* coef, int R, int n0, int* cnt, int2* pairs) {
+  const int nn = n0 * n0, ns = coef_stride(n0);
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    int n = 0;
+    for (int e = 0; e < nn; ++e) {
+      const float c = coef[r * ns + e];
+      if (c != 0.f) pairs[r * nn + n++] = make_int2(e, __float_as_int(c));
+    }
+    cnt[r] = n;
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void stage_store(float* p, const float (&x)[VEC]) {
+  store_vec<float, VEC>(p, x);
+}
+template <int VEC>
+__device__ __forceinline__ void stage_load(float (&x)[VEC], const float* p) {
+  load_vec<float, VEC>(x, p);
+}
+
+template <int N0, int VEC, bool FAST>
+__global__ void __launch_bounds__(kThreadsX) decode_sparse_kernel(const __grid_constant__ Tables<float> t,
+                                                                  const PassArgs a) {
+  constexpr int NN = N0 * N0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int R = t.R;
+  const SparseSmem lay(R, N0, VEC);
+  float* coef = reinterpret_cast<float*>(smem_raw);
+  int* cnt = reinterpret_cast<int*>(smem_raw + lay.cnt);
+  const int2* pairs = reinterpret_cast<const int2*>(smem_raw + lay.pairs);
+  float* stage = reinterpret_cast<float*>(smem_raw + lay.stage) + threadIdx.x * VEC;
+  const int64_t colsv = (a.xcol + VEC - 1) / VEC * VEC;
+  const int64_t pos = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
+  const int64_t y = pos / colsv, x = pos - y * colsv;
+  const int64_t xs = x % a.seg, avail = a.mval - xs;
+  const bool valid = y < a.nb && x < a.xcol && avail > 0;
+  const int64_t xdst = a.plain ? logical_col(x, a.seg, a.mval) : x;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  const int64_t avail_st = FAST ? VEC : (a.plain ? avail : VEC);
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    __syncthreads();
+    expand_subtree(t, a, 1, 2, p, coef);
+    __syncthreads();
+    build_lists(coef, R, N0, cnt, const_cast<int2*>(pairs));
+    __syncthreads();
+    if (!valid) continue;
+    DecodeFetch<float, float, VEC> fetch;
+    fetch.M = static_cast<const float*>(a.X) + p * a.outs_per_parent * a.strideX;
+    fetch.strideM = a.strideX;
+    fetch.off = y * a.ldx + x;
+    fetch.avail = FAST ? VEC : avail;
+    fetch.vec = FAST || a.vload != 0;
+    {
+      float z[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) z[v] = 0.f;
+#pragma unroll
+      for (int e = 0; e < NN; ++e) stage_store<VEC>(stage + e * kThreadsX * VEC, z);
+    }
+    constexpr int B = 4;  // children loaded together (8 spilled registers and measured slower)
+    for (int r0 = 0; r0 < R; r0 += B) {
+      float m[B][VEC];
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        if (r0 + b < R) fetch(r0 + b, m[b]);
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int r = r0 + b, n = r < R ? cnt[r] : 0;
+        for (int i = 0; i < n; ++i) {
+          const int2 pr = pairs[r * NN + i];
+          const float c = __int_as_float(pr.y);
+          float* sp = stage + pr.x * kThreadsX * VEC;
+          float acc[VEC];
+          stage_load<VEC>(acc, sp);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[v] = acc[v] + c * m[b][v];
+          stage_store<VEC>(sp, acc);
+        }
+      }
+    }
+    float* P = static_cast<float*>(a.Y) + p * a.strideY;
+    const bool vs = FAST || a.vstore != 0;
+#pragma unroll
+    for (int k = 0; k < N0; ++k)
+#pragma unroll
+      for (int l = 0; l < N0; ++l) {
+        float o[VEC];
+        stage_load<VEC>(o, stage + (k * N0 + l) * kThreadsX * VEC);
+        store_some<float, VEC>(P + (k * a.nb + y) * a.ldy + l * colstep + xdst, o, vs, avail_st);
+      }
+  }
+}
+
 inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
   const int64_t span = (int64_t)kThreadsX * vec;
@@ -628,6 +744,14 @@ cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   a.vload = a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tm));
   a.vstore = yalign && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
   const bool fast = a.vload && a.vstore && a.mval % VEC == 0;
+  if constexpr (sizeof(Tc) == 4 && sizeof(Tm) == 4 && sizeof(To) == 4 && G == 1 && N0 >= 3) {
+    const SparseSmem lay(t.R, N0, VEC);
+    auto kern = fast ? decode_sparse_kernel<N0, VEC, true> : decode_sparse_kernel<N0, VEC, false>;
+    cudaError_t e = prep(kern, lay.total);
+    if (e != cudaSuccess) return e;
+    kern<<<pass_grid(a.nb, a.xcol, a.parents, VEC), kThreadsX, lay.total, st>>>(t, a);
+    return cudaGetLastError();
+  }
   auto kern = fast ? decode_pass_kernel<Tm, To, Tc, N0, G, VEC, true> : decode_pass_kernel<Tm, To, Tc, N0, G, VEC, false>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
