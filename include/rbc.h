@@ -98,6 +98,10 @@ typedef struct {
   double gamma;        /* Eq. square-root-of-sum                                      */
   double scale;        /* (1 - kappa)^{-1} if rescaled, else 1                         */
   uint64_t seed;
+  /* 1: U, V, W are exactly Strassen's formula, 2: exactly Laderman's (the two formulas of
+   * Section 1, in the forms of the library's built-in tables); 0: any other formula.  The
+   * built-in formulas run one-level passes with their sparsity compiled in. */
+  int builtin_formula;
 } rbc_plan_info;
 
 /* Draws (Section 2.1).  Counter-based: draw set `key` uses the six words

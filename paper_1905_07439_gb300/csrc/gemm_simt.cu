@@ -129,8 +129,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // S and T is zero and is skipped).  A CTA stages the S and T operands of `nl` consecutive
 // leaves (contiguous ranges of the leaf buffers) in shared memory; each thread computes 2 x 2
 // output blocks of the first 2 ceil(m/2) rows and columns, summing over k in order as the
-// tiled kernel does.  Modes 0 (store M; rows and columns past those are left unwritten and
-// are never read) and 2 (store C, L = 0).
+// tiled kernel does.  Modes 0 (store M, its padding rows and columns set to zero like the
+// tiled kernels' products of zero-padded operands) and 2 (store C, L = 0).
 constexpr int kSmallThreads = 128;
 
 template <typename T>
@@ -152,6 +152,13 @@ __global__ void __launch_bounds__(kSmallThreads) simt_small_gemm_kernel(const Si
       sT[e] = Tg[e];
     }
     __syncthreads();
+    if (a.mode == 0) {  // zero padding of M beyond the computed 2 ceil(m/2) rows and columns
+      const int mc = 2 * hb;
+      for (int e = threadIdx.x; e < cnt * per; e += kSmallThreads) {
+        const int lf = e / per, rc = e - lf * per, r = rc / mp, c = rc - r * mp;
+        if (r >= mc || c >= mc) static_cast<T*>(a.out)[(l0 + lf) * a.strideO + r * a.ldo + c] = (T)0;
+      }
+    }
     for (int u = threadIdx.x; u < cnt * units; u += kSmallThreads) {
       const int lf = u / units, rem = u - lf * units, bi = rem / hb, bj = rem - bi * hb;
       const T* sr = sS + lf * per + 2 * bi * mp;

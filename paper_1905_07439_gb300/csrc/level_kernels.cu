@@ -22,7 +22,10 @@
 
 #include <cstring>
 
+#include <type_traits>
+
 #include "convert.cuh"
+#include "formulas.h"
 #include "level_kernels.cuh"
 #include "rbc_internal.h"
 
@@ -666,6 +669,190 @@ __global__ void __launch_bounds__(kThreadsX) decode_sparse_kernel(const __grid_c
   }
 }
 
+// ------------------------------------------------------------------ built-in formulas, one level
+// One-level passes of the built-in formulas (Strassen, Laderman).  The node's signed
+// permutations act on the operands, and the base formula's sparsity is compiled in:
+//   S_r = sum_{k,l} u_{pi1(k) pi2(l) r} s1(k) s2(l) A_kl
+//       = sum_{(k',l'): u_{k'l'r} != 0} u_{k'l'r} [s1(k) s2(l) A_kl]_{k = pi1^-1(k'), l = pi2^-1(l')}
+// (likewise T_r with pi2, pi3, s2, s3), so a thread loads the sub-blocks in permuted order with
+// their signs and adds the formula's nonzero terms; and
+//   C_ij = scale s1(i) s3(j) D_{pi1(i) pi3(j)},   D_{i'j'} = sum_r w_{i'j'r} M_r,
+// so the decode sums the nonzero terms of D (children in order) and stores D_{i'j'} into block
+// (pi1^-1(i'), pi3^-1(j')).  No coefficient table is expanded and no zero term is evaluated.
+
+template <int I, int N, class Fn>
+__device__ __forceinline__ void static_for(Fn&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// Draw set of launch parent p (the root of its one-level subtree).
+template <typename Tc>
+__device__ __forceinline__ uint64_t parent_draw(const Tables<Tc>& t, const PassArgs& a, int64_t p) {
+  int64_t real = 0, hp = a.node_first + p;
+  if (a.real_parents > 0) {
+    real = p / a.real_parents;
+    hp = a.node_first + (p - real * a.real_parents);
+  }
+  const uint64_t* draws = t.draw + real * a.real_draws;
+  return t.per_level ? draws[a.depth] : draws[a.dbase[0] + (hp - a.dfirst[0])];
+}
+
+// inv[k'] = pi_c^-1(k') and sg[k'] = s_c(pi_c^-1(k')) of stream c of a draw set.
+template <typename Tc, int N0>
+__device__ __forceinline__ void inverse_stream(uint64_t w, int c, int (&inv)[N0], Tc (&sg)[N0]) {
+#pragma unroll
+  for (int kp = 0; kp < N0; ++kp) {
+    int src = 0;
+#pragma unroll
+    for (int j = 0; j < N0; ++j)
+      if (draw_perm(w, c, j) == kp) src = j;
+    inv[kp] = src;
+    sg[kp] = (Tc)draw_sign(w, c, src);
+  }
+}
+
+template <typename Tin, typename Tc, class F, int TENSOR, int S, int VEC, bool FAST>
+__global__ void __launch_bounds__(kThreadsX) encode_fixed_kernel(const __grid_constant__ Tables<Tc> t,
+                                                                 const PassArgs a) {
+  constexpr int N0 = F::n0, R = F::R, NN = N0 * N0;
+  constexpr int CR = TENSOR == 1 ? 1 : 0, CC = TENSOR == 0 ? 1 : 2;  // row / column streams
+  using Tout = typename StoreType<S>::T;
+  const int64_t colsv = (a.cols_out + VEC - 1) / VEC * VEC;
+  const int64_t pos = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
+  const int64_t y = pos / colsv, x = pos - y * colsv;
+  if (y >= a.rows_out || x >= a.cols_out) return;
+  const int64_t outs = a.outs_per_parent;
+  const int64_t xs = x % a.seg;
+  const int64_t avail_in = a.mval - xs;
+  const int64_t xsrc = a.plain ? logical_col(x, a.seg, a.mval) : x;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  const bool padding = y >= a.nb || avail_in <= 0;
+  const bool full = FAST || (a.vload && avail_in >= VEC);
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    EncodeEmitV<Tc, S, VEC> emit;
+    emit.Y = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
+    emit.strideY = a.strideY;
+    emit.off = y * a.ldy + x;
+    emit.kpanel = a.kpanel;
+    emit.split = a.split;
+    emit.vec = FAST || a.vstore != 0;
+    emit.avail = FAST ? VEC : a.cols_out - x;
+    if (padding) {  // zero outputs
+      Tc z[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) z[v] = (Tc)0;
+      for (int64_t q = 0; q < outs; ++q) emit(q, z);
+      continue;
+    }
+    const uint64_t w = parent_draw(t, a, p);
+    int ir[N0], ic[N0];
+    Tc sr[N0], sc[N0];
+    inverse_stream<Tc, N0>(w, CR, ir, sr);
+    inverse_stream<Tc, N0>(w, CC, ic, sc);
+    const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
+    Tc in[NN][VEC];  // in[k' n0 + l'] = s s' X(pi^-1(k'), pi'^-1(l'))
+#pragma unroll
+    for (int kp = 0; kp < N0; ++kp)
+#pragma unroll
+      for (int lp = 0; lp < N0; ++lp) {
+        const Tin* src = X + (ir[kp] * a.nb + y) * a.ldx + ic[lp] * colstep + xsrc;
+        Tin raw[VEC];
+        if (full) {
+          load_vec<Tin, VEC>(raw, src);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) raw[v] = (v < avail_in) ? src[v] : (Tin)0;
+        }
+        const Tc sg = sr[kp] * sc[lp];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) in[kp * N0 + lp][v] = sg * (Tc)raw[v];
+      }
+    static_for<0, R>([&](auto rr) {
+      constexpr int r = decltype(rr)::value;
+      Tc acc[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[v] = (Tc)0;
+      static_for<0, NN>([&](auto ee) {
+        constexpr int e = decltype(ee)::value;
+        constexpr int c = TENSOR == 0 ? F::U[e * R + r] : F::V[e * R + r];
+        if constexpr (c != 0) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[v] = acc[v] + (Tc)c * in[e][v];
+        }
+      });
+      emit(r, acc);
+    });
+  }
+}
+
+template <typename Tc, class F, int VEC, bool FAST>
+__global__ void __launch_bounds__(kThreadsX) decode_fixed_kernel(const __grid_constant__ Tables<Tc> t,
+                                                                 const PassArgs a) {
+  constexpr int N0 = F::n0, R = F::R, NN = N0 * N0, B = 4;
+  const int64_t colsv = (a.xcol + VEC - 1) / VEC * VEC;
+  const int64_t pos = ((int64_t)blockIdx.x * kThreadsX + threadIdx.x) * VEC;
+  const int64_t y = pos / colsv, x = pos - y * colsv;
+  const int64_t xs = x % a.seg, avail = a.mval - xs;
+  if (!(y < a.nb && x < a.xcol && avail > 0)) return;
+  const int64_t xdst = a.plain ? logical_col(x, a.seg, a.mval) : x;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  const int64_t avail_st = FAST ? VEC : (a.plain ? avail : VEC);
+  const bool vs = FAST || a.vstore != 0;
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    DecodeFetch<Tc, Tc, VEC> fetch;
+    fetch.M = static_cast<const Tc*>(a.X) + p * a.outs_per_parent * a.strideX;
+    fetch.strideM = a.strideX;
+    fetch.off = y * a.ldx + x;
+    fetch.avail = FAST ? VEC : avail;
+    fetch.vec = FAST || a.vload != 0;
+    Tc D[NN][VEC];
+#pragma unroll
+    for (int e = 0; e < NN; ++e)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) D[e][v] = (Tc)0;
+    static_for<0, (R + B - 1) / B>([&](auto gg) {
+      constexpr int r0 = decltype(gg)::value * B;
+      Tc m[B][VEC];
+      static_for<0, B>([&](auto bb) {
+        constexpr int b = decltype(bb)::value;
+        if constexpr (r0 + b < R) fetch(r0 + b, m[b]);
+      });
+      static_for<0, B>([&](auto bb) {
+        constexpr int b = decltype(bb)::value;
+        if constexpr (r0 + b < R) {
+          static_for<0, NN>([&](auto ee) {
+            constexpr int e = decltype(ee)::value;
+            constexpr int c = F::W[e * R + r0 + b];
+            if constexpr (c != 0) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) D[e][v] = D[e][v] + (Tc)c * m[b][v];
+            }
+          });
+        }
+      });
+    });
+    const uint64_t w = parent_draw(t, a, p);
+    int ir[N0], ic[N0];
+    Tc sr[N0], sc[N0];
+    inverse_stream<Tc, N0>(w, 0, ir, sr);
+    inverse_stream<Tc, N0>(w, 2, ic, sc);
+    Tc* P = static_cast<Tc*>(a.Y) + p * a.strideY;
+#pragma unroll
+    for (int ip = 0; ip < N0; ++ip)
+#pragma unroll
+      for (int jp = 0; jp < N0; ++jp) {
+        const Tc f = t.scale * sr[ip] * sc[jp];
+        Tc o[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = f * D[ip * N0 + jp][v];
+        store_some<Tc, VEC>(P + (ir[ip] * a.nb + y) * a.ldy + ic[jp] * colstep + xdst, o, vs, avail_st);
+      }
+  }
+}
+
 inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
   const int64_t span = (int64_t)kThreadsX * vec;
@@ -702,7 +889,23 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   const bool xalign = a.plain ? (a.nb % VEC == 0 && (a.mval % VEC == 0 || a.cols_out <= a.seg)) : a.xcol % VEC == 0;
   a.vload = xalign && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
   a.vstore = a.ldy % VEC == 0 && a.strideY % VEC == 0 && a.kpanel % VEC == 0 && aligned(a.Y, VEC * sizeof(Tout));
-  const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0 && a.mval % VEC == 0;
+  // The passes write zeros into every padding column of the intermediates, so whole vectors
+  // read from a padded-layout input are exact even where they run past the valid columns.
+  const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0 && (a.plain ? a.mval % VEC == 0 : true);
+  if constexpr (G == 1 && (N0 == 2 || N0 == 3)) {
+    using F = std::conditional_t<N0 == 2, StrassenFormula, LadermanFormula>;
+    if (a.formula == F::id) {
+      const dim3 grid = pass_grid(a.rows_out, a.cols_out, a.parents, VEC);
+      if (a.tensor == 0) {
+        if (fast) encode_fixed_kernel<Tin, Tc, F, 0, S, VEC, true><<<grid, kThreadsX, 0, st>>>(t, a);
+        else encode_fixed_kernel<Tin, Tc, F, 0, S, VEC, false><<<grid, kThreadsX, 0, st>>>(t, a);
+      } else {
+        if (fast) encode_fixed_kernel<Tin, Tc, F, 1, S, VEC, true><<<grid, kThreadsX, 0, st>>>(t, a);
+        else encode_fixed_kernel<Tin, Tc, F, 1, S, VEC, false><<<grid, kThreadsX, 0, st>>>(t, a);
+      }
+      return cudaGetLastError();
+    }
+  }
   auto kern = fast ? encode_pass_kernel<Tin, Tc, N0, G, S, VEC, true> : encode_pass_kernel<Tin, Tc, N0, G, S, VEC, false>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
@@ -743,7 +946,19 @@ cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   const bool yalign = a.plain ? (a.nb % VEC == 0 && (a.mval % VEC == 0 || a.xcol <= a.seg)) : true;
   a.vload = a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tm));
   a.vstore = yalign && a.ldy % VEC == 0 && a.strideY % VEC == 0 && aligned(a.Y, VEC * sizeof(To));
-  const bool fast = a.vload && a.vstore && a.mval % VEC == 0;
+  // Children (leaf products and padded-layout intermediates) hold zeros in their padding
+  // columns, so whole-vector loads are exact; a padded-layout parent takes whole-vector
+  // stores, a plain one (C) only complete vectors.
+  const bool fast = a.vload && a.vstore && (a.plain ? a.mval % VEC == 0 : true);
+  if constexpr (G == 1 && (N0 == 2 || N0 == 3) && std::is_same_v<Tm, Tc> && std::is_same_v<To, Tc>) {
+    using F = std::conditional_t<N0 == 2, StrassenFormula, LadermanFormula>;
+    if (a.formula == F::id) {
+      const dim3 grid = pass_grid(a.nb, a.xcol, a.parents, VEC);
+      if (fast) decode_fixed_kernel<Tc, F, VEC, true><<<grid, kThreadsX, 0, st>>>(t, a);
+      else decode_fixed_kernel<Tc, F, VEC, false><<<grid, kThreadsX, 0, st>>>(t, a);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (sizeof(Tc) == 4 && sizeof(Tm) == 4 && sizeof(To) == 4 && G == 1 && N0 >= 3) {
     const SparseSmem lay(t.R, N0, VEC);
     auto kern = fast ? decode_sparse_kernel<N0, VEC, true> : decode_sparse_kernel<N0, VEC, false>;

@@ -49,6 +49,7 @@ struct PassArgs {
   int64_t real_draws;
   int depth;
   int tensor;     // encode: 0 left operand (u^), 1 right operand (v^)
+  int formula;    // rbc::BuiltinFormula of the plan's U, V, W (compiled-in one-level passes)
   int split;      // encode: write [hi | lo] panels
   int trans;      // encode, last pass: write each output transposed
   int vload;      // set by the launcher: input rows allow VEC-wide vector loads

@@ -270,6 +270,7 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
       PassArgs a{};
       rbc_status s2 = launch_tables(rs, d, g, k0, kc, c0, cnt, &a, tab);
       if (s2 != RBC_OK) return s2;
+      a.formula = p->builtin;
       const int64_t first = k0 * P + c0;  // first parent of the launch, realization-major
       if (d == 0) {  // the caller's matrix, plain layout
         a.X = X;
@@ -332,6 +333,7 @@ rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc
       PassArgs a{};
       rbc_status s2 = launch_tables(rs, d, g, k0, kc, c0, cnt, &a, tab);
       if (s2 != RBC_OK) return s2;
+      a.formula = p->builtin;
       const int64_t first = k0 * P + c0;
       if (bottom) {  // leaf products: rows of mp >= seg columns
         a.X = ws + lo.M + (size_t)first * outs * lo.mp * lo.mp * lo.es_acc;

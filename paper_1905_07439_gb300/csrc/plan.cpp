@@ -5,9 +5,24 @@
 #include <mutex>
 #include <new>
 
+#include "formulas.h"
 #include "rbc_internal.h"
 
 namespace rbc {
+
+// The built-in formula that U, V, W equal exactly, if any.
+template <class F>
+static bool equals_formula(const rbc_plan_s* p) {
+  if (p->n0 != F::n0 || p->R != F::R) return false;
+  for (int e = 0; e < F::n0 * F::n0 * F::R; ++e)
+    if (p->U[e] != (double)F::U[e] || p->V[e] != (double)F::V[e] || p->W[e] != (double)F::W[e]) return false;
+  return true;
+}
+static int builtin_formula(const rbc_plan_s* p) {
+  if (equals_formula<StrassenFormula>(p)) return kFormulaStrassen;
+  if (equals_formula<LadermanFormula>(p)) return kFormulaLaderman;
+  return kFormulaGeneric;
+}
 
 static thread_local std::string g_last_error;
 
@@ -211,6 +226,7 @@ rbc_status rbc_plan_create_ex(const rbc_plan_desc* d, rbc_plan_t* out) {
     return fail(RBC_EKAPPA, "kappa == 1: the randomized formula is undefined");
   }
   p->tau = formula_tau(p);
+  p->builtin = builtin_formula(p);
   p->gamma = formula_gamma(p);
   const bool rescale = d->rescale_kappa == -1 ? d->rand_mode != RBC_RAND_NONE : d->rescale_kappa == 1;
   p->scale = rescale ? 1.0 / (1.0 - p->kappa) : 1.0;
@@ -269,6 +285,7 @@ rbc_status rbc_plan_query(rbc_plan_t p, rbc_plan_info* info) {
   info->gamma = p->gamma;
   info->scale = p->scale;
   info->seed = p->seed;
+  info->builtin_formula = p->builtin;
   return RBC_OK;
 }
 

@@ -55,6 +55,7 @@ __host__ __device__ __forceinline__ int draw_sign(uint64_t w, int c, int j) {
 
 struct rbc_plan_s {
   int R = 0, n0 = 0, L = 0, mode = 0, scope = 0, rescale = -1;
+  int builtin = 0;  // rbc::BuiltinFormula of U, V, W
   uint64_t seed = 0;
   std::vector<double> U, V, W;
   double kappa = 0, tau = 0, gamma = 0, scale = 1;

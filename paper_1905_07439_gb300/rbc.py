@@ -34,7 +34,7 @@ class rbc_plan_info(C.Structure):
     _fields_ = [("R", C.c_int), ("n0", C.c_int), ("levels", C.c_int), ("rand_mode", C.c_int),
                 ("draw_scope", C.c_int), ("draw_count", C.c_int64), ("leaf_count", C.c_int64),
                 ("kappa", C.c_double), ("tau", C.c_double), ("gamma", C.c_double),
-                ("scale", C.c_double), ("seed", C.c_uint64)]
+                ("scale", C.c_double), ("seed", C.c_uint64), ("builtin_formula", C.c_int)]
 
 
 class rbc_group_item(C.Structure):

@@ -122,3 +122,17 @@ def test_workspace_sizes(rbc):
     p4 = rbc.Plan(U, V, W, levels=4)
     ws4 = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
     assert ws4 >= 2 * 4 * 7 * 4096**2 + 2 * 2 * 2401 * 512**2
+
+
+def test_builtin_formulas_are_recognised(rbc):
+    """The library recognises exactly the Strassen and Laderman tensors (Section 1) and runs
+    their one-level passes with compiled-in sparsity; any other formula is generic."""
+    from rbc_inputs import formula_by_name, laderman, perturbed, strassen
+    assert rbc.Plan(*strassen(), levels=1).info()["builtin_formula"] == 1
+    assert rbc.Plan(*laderman(), levels=1).info()["builtin_formula"] == 2
+    assert rbc.Plan(*formula_by_name("noisy-strassen"), levels=1).info()["builtin_formula"] == 0
+    assert rbc.Plan(*perturbed(*laderman(), seed=3), levels=1).info()["builtin_formula"] == 0
+    U, V, W = strassen()
+    W = W.copy()
+    W[0, 0, 0] = 2.0  # one coefficient changed: generic
+    assert rbc.Plan(U, V, W, levels=1).info()["builtin_formula"] == 0
