@@ -229,7 +229,7 @@ def run_ours(args):
 
     # Leaf-product kernel (with fused decode): the dominant kernel.
     leaf_ms, leaf_flops, enc_ms, enc_bytes = 0.0, 0.0, 0.0, 0.0
-    per_case = []
+    per_case, case_model = [], []
     es_leaf = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2}[args.leaf]
     split = 3 if args.leaf.startswith("3x") else 1      # MMA passes per leaf product
     panels = 2 if args.leaf.startswith("3x") else 1     # stored operand panels (hi, lo)
@@ -253,6 +253,7 @@ def run_ours(args):
                          "leaf_ms": round(g, 3), "leaf_tflops": round(lf / g / 1e9, 2),
                          "encode_ms": round(e, 3), "encode_gbs": round(eb / e / 1e6, 1),
                          "decode_ms": round(dec, 3)})
+        case_model.append((lf, eb + es_leaf * panels * 2 * R**L * m * m + 4 * n * n + 4 * 2 * R**L * m * m, tot))
     pk, pk_kind = peaks()
     if args.leaf in ("f32",):
         bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
@@ -273,6 +274,15 @@ def run_ours(args):
             "peak_source": peak_note,
             "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
                        "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}}
+    # Whole-call model: leaf flops at the peak beside the algorithmic bytes (read A, B; write and
+    # read the leaf operands; write and read M; write C) at the measured HBM bandwidth.
+    t_sum = sum(f / (peak * 1e12) + b / (pk["hbm_gbs"] * 1e9) for f, b, _ in case_model) * 1e3
+    t_max = sum(max(f / (peak * 1e12), b / (pk["hbm_gbs"] * 1e9)) for f, b, _ in case_model) * 1e3
+    roof["whole_call"] = {"ms_measured": round(sum(t for _, _, t in case_model), 3),
+                          "ms_model_sum": round(t_sum, 3), "ms_model_max": round(t_max, 3),
+                          "frac_of_sum_model": round(t_sum / sum(t for _, _, t in case_model), 4),
+                          "note": "model_sum = leaf flops / peak + algorithmic bytes / HBM per case; "
+                                  "model_max takes the larger of the two per case"}
     launches_per_step = sum(counts) // max(1, args.steps)
 
     # End to end through the public API: H2D of A and B, the call, D2H of C, per case.
