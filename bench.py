@@ -299,7 +299,7 @@ def run_ours(args):
             "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": None,
             "traffic_note": "per-launch DRAM bytes differ per case; the ncu capture of one launch is summarized "
-                            "in profiles/tc_gemm_noisy_strassen_n4096_L1_3xbf16.md",
+                            "in profiles/tc_gemm_3xbf16_leaves.md",
             "peak_source": peak_note,
             "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
                        "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}}
