@@ -314,16 +314,45 @@ def run_ours(args):
                                   "model_max takes the larger of the two per case"}
     launches_per_step = sum(counts) // max(1, args.steps)
 
-    # End to end through the public API: H2D of A and B, the call, D2H of C, per case.
+    # End to end through the public API: per product, H2D of A and B from pinned host memory,
+    # the call, D2H of C.  The copies run on their own streams with two device buffer sets, so
+    # that one product's copies overlap the previous product's computation.
     e2e = None
     if not args.no_e2e:
+        h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        dbuf = [{n: {"A": inputs[n]["A"], "B": inputs[n]["B"], "C": inputs[n]["C"]} for n in inputs},
+                {n: {k: torch.empty_like(inputs[n]["A"]) for k in ("A", "B", "C")} for n in inputs}]
+        hout = [{n: inputs[n]["hC"] for n in inputs},
+                {n: torch.empty_like(inputs[n]["hC"]).pin_memory() for n in inputs}]
+
         def e2e_step():
-            for plan, (nm, n, L) in zip(plans, cases):
-                x = inputs[n]
-                x["A"].copy_(x["hA"], non_blocking=True)
-                x["B"].copy_(x["hB"], non_blocking=True)
-                rbc.matmul(plan, x["A"], x["B"], x["C"], leaf=leaf, workspace=ws, decode=args.decode)
-                x["hC"].copy_(x["C"], non_blocking=True)
+            start = torch.cuda.Event()
+            start.record(stream)
+            h2d.wait_event(start)
+            d2h.wait_event(start)
+            ev_c, ev_d = {}, {}
+            for i, (plan, (nm, n, L)) in enumerate(zip(plans, cases)):
+                k, x = i % 2, inputs[n]
+                d = dbuf[k][n]
+                if i >= 2:
+                    h2d.wait_event(ev_c[i - 2])  # product i-2 no longer reads this buffer set
+                with torch.cuda.stream(h2d):
+                    d["A"].copy_(x["hA"], non_blocking=True)
+                    d["B"].copy_(x["hB"], non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(h2d)
+                stream.wait_event(ev_in)
+                if i >= 2:
+                    stream.wait_event(ev_d[i - 2])  # product i-2's result has left this C
+                rbc.matmul(plan, d["A"], d["B"], d["C"], leaf=leaf, workspace=ws, decode=args.decode, stream=stream)
+                ev_c[i] = torch.cuda.Event()
+                ev_c[i].record(stream)
+                d2h.wait_event(ev_c[i])
+                with torch.cuda.stream(d2h):
+                    hout[k][n].copy_(d["C"], non_blocking=True)
+                ev_d[i] = torch.cuda.Event()
+                ev_d[i].record(d2h)
+            stream.wait_event(ev_d[len(cases) - 1])  # the step ends with its last result on the host
         e2e_step()
         barrier()
         a0 = torch.cuda.Event(enable_timing=True)
