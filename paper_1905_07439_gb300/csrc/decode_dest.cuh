@@ -24,7 +24,7 @@ struct DestList {
 };
 
 // Build the per-level nonzero lists of `leaf` (one thread).  The tables must hold every
-// draw set of the tree (draw_base 0).
+// draw set of the tree from the root on (draw[heap id], or draw[depth] per level).
 template <typename T>
 __device__ inline void build_dest_list(const Tables<T>& t, int64_t leaf, DestList<T>& d) {
   const int L = t.L, R = t.R, n0 = t.n0;

@@ -153,33 +153,10 @@ rbc_status fill_tables(const rbc_plan_s* p, int64_t key_first, int64_t count, Ta
   t->R = p->R;
   t->L = p->L;
   t->per_level = p->scope == RBC_DRAW_PER_LEVEL;
-  t->draw_base = key_first;
   return RBC_OK;
 }
 template rbc_status fill_tables<float>(const rbc_plan_s*, int64_t, int64_t, Tables<float>*);
 
-template <typename T>
-rbc_status fill_tables_ranges(const rbc_plan_s* p, const int64_t* first, const int64_t* count, int nranges,
-                              Tables<T>* t) {
-  int64_t total = 0;
-  for (int i = 0; i < nranges; ++i) {
-    if (first[i] < 0 || count[i] < 0 || first[i] + count[i] > p->draw_count)
-      return fail(RBC_EINVAL, "draw range out of bounds");
-    total += count[i];
-  }
-  if (total > kMaxDraws)
-    return fail(RBC_EUNSUPPORTED, "one launch needs more than 1024 draw sets");
-  rbc_status s = fill_tables(p, 0, 0, t);
-  if (s != RBC_OK) return s;
-  int64_t o = 0;
-  for (int i = 0; i < nranges; ++i)
-    for (int64_t k = 0; k < count[i]; ++k) t->draw[o++] = p->packed[first[i] + k];
-  return RBC_OK;
-}
-template rbc_status fill_tables_ranges<float>(const rbc_plan_s*, const int64_t*, const int64_t*, int,
-                                              Tables<float>*);
-template rbc_status fill_tables_ranges<double>(const rbc_plan_s*, const int64_t*, const int64_t*, int,
-                                               Tables<double>*);
 template rbc_status fill_tables<double>(const rbc_plan_s*, int64_t, int64_t, Tables<double>*);
 
 }  // namespace rbc

@@ -38,8 +38,7 @@ struct Tables {
   uint64_t draw[kMaxDraws];
   T scale;
   int n0, R, L;
-  int per_level;      // 1: draw index = depth; 0: draw index = heap node id - draw_base
-  int64_t draw_base;  // heap id of draw[0] (per-node scope)
+  int per_level;      // 1: one draw set per depth; 0: one per node (the launch's PassArgs locate them)
 };
 
 #if defined(__CUDACC__)
@@ -90,9 +89,5 @@ void packed_draws(const rbc_plan_s* p, uint64_t seed, uint64_t* out);
 // Fill the tables of a launch touching draw sets [key_first, key_first + count).
 template <typename T>
 rbc_status fill_tables(const rbc_plan_s* p, int64_t key_first, int64_t count, Tables<T>* t);
-// Same with the concatenation of several ranges [first[i], first[i] + count[i]).
-template <typename T>
-rbc_status fill_tables_ranges(const rbc_plan_s* p, const int64_t* first, const int64_t* count, int nranges,
-                              Tables<T>* t);
 
 }  // namespace rbc

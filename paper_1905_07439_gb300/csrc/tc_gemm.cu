@@ -428,7 +428,6 @@ uint32_t leaf_idesc(int leaf, int bn) {
 }  // namespace
 
 int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
-bool tc_supports_store_m() { return true; }
 
 int tc_default_bn(int leaf, int64_t mp) {
   const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;

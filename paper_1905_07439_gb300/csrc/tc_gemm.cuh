@@ -51,7 +51,6 @@ struct TcGroupArgs {
 };
 
 int64_t tc_pad(int64_t m);
-bool tc_supports_store_m();
 int tc_default_bn(int leaf, int64_t mp);
 int tc_default_group(int leaf, int64_t mp, int64_t K);
 // Fill the descriptor and the two tensor maps (host memory, 128 bytes) of one instance.
