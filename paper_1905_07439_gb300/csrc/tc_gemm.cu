@@ -33,6 +33,10 @@ namespace {
 constexpr int BM = 128;
 constexpr int kRowBytes = 128;  // one swizzle row: 64 bf16/f16 or 32 tf32 elements of K
 constexpr int kThreads = 192;
+// Epilogue staging of stored products: one 32 x 32 fp32 block per epilogue warp, rows padded
+// to 36 floats (16-byte aligned rows, four-way bank spread).
+constexpr int kStageLd = 36;
+constexpr size_t kStageBytes = 4 * 32 * kStageLd * sizeof(float);
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct Params {
@@ -114,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Aux<STAGES>* aux = reinterpret_cast<Aux<STAGES>*>(smem + STAGES * STAGE_BYTES);
+  float* ostage = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + ((sizeof(Aux<STAGES>) + 15) & ~(size_t)15));
   volatile int* abort = &aux->abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -298,10 +303,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int64_t col0 = (int64_t)tn * BN + c0;
         if (d.epi == 2) {
-          float* dst = d.M + leaf * d.strideM + row * d.ldm + col0;
+          // Through shared memory, so that every store instruction writes four whole 128-byte
+          // row segments (a lane holds one row; the block is re-read by rows).
+          float* sb = ostage + (warp - 2) * 32 * kStageLd;
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            *reinterpret_cast<float4*>(sb + lane * kStageLd + 4 * q) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          __syncwarp();
+          const int64_t row0 = (int64_t)tm * BM + quarter * 32;
+          float* dstb = d.M + leaf * d.strideM + row0 * d.ldm + col0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int r = j * 4 + (lane >> 3), c = (lane & 7) * 4;
+            *reinterpret_cast<float4*>(dstb + r * d.ldm + c) = *reinterpret_cast<const float4*>(sb + r * kStageLd + c);
+          }
+          __syncwarp();  // the block is read before the next chunk overwrites it
           continue;
         }
         if (row >= d.m) continue;
@@ -377,7 +394,8 @@ template <int KIND, int SPLIT, int BN, int STAGES, bool GROUPED>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t, const Params& p,
                    cudaStream_t st) {
   constexpr int P = SPLIT ? 2 : 1;
-  constexpr size_t smem = (size_t)STAGES * P * (BM + BN) * kRowBytes + sizeof(Aux<STAGES>) + 1024;
+  constexpr size_t smem =
+      (size_t)STAGES * P * (BM + BN) * kRowBytes + ((sizeof(Aux<STAGES>) + 15) & ~(size_t)15) + kStageBytes + 1024;
   static_assert(smem <= 232448, "shared memory budget");
   auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES, GROUPED>;
   int dev = 0, sms = 0;
