@@ -10,9 +10,11 @@
 //              tcgen05.mma (M = 128, N = BN, K = 16 bf16/f16 or 8 tf32 per instruction),
 //              committing stage releases and accumulator-ready signals;
 //   warps 2-5  drain an accumulator with tcgen05.ld (one TMEM lane = one tile row per
-//              thread) while the MMA fills the other, and scatter the tile into every C block
-//              it feeds: C_IJ += (prod_d w^(node_d)_{i_d j_d r_d}) * M_tile, by 16-byte
-//              vector reductions into the zeroed C (or plain stores when L = 0 / stored M).
+//              thread) while the MMA fills the other; each 32 x 32 block passes through
+//              shared memory so that the global writes cover whole row segments; they scatter
+//              the tile into every C block it feeds: C_IJ += (prod_d w^(node_d)_{i_d j_d r_d})
+//              * M_tile, by 16-byte vector reductions into the zeroed C (or plain stores when
+//              L = 0 / stored M).
 // Split-compensated modes keep hi and lo panels of each operand in a stage and issue
 // hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator.
 // Every mbarrier wait is bounded (2 s); on expiry the kernel records RBC_ETIMEOUT in the
@@ -290,7 +292,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncwarp();
       ptx::tc_fence_after();
-      const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
@@ -302,50 +303,64 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) ptx::mbar_arrive(&aux->tempty[buf]);
         }
         const int64_t col0 = (int64_t)tn * BN + c0;
-        if (d.epi == 2) {
-          // Through shared memory, so that every store instruction writes four whole 128-byte
-          // row segments (a lane holds one row; the block is re-read by rows).
-          float* sb = ostage + (warp - 2) * 32 * kStageLd;
+        // Every output goes through shared memory, so that each store (or reduction)
+        // instruction covers four whole 128-byte row segments: a lane holds one row of the
+        // accumulator, and the 32 x 32 block is re-read by rows.
+        float* sb = ostage + (warp - 2) * 32 * kStageLd;
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            *reinterpret_cast<float4*>(sb + lane * kStageLd + 4 * q) =
-                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          __syncwarp();
-          const int64_t row0 = (int64_t)tm * BM + quarter * 32;
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(sb + lane * kStageLd + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+        const int64_t row0 = (int64_t)tm * BM + quarter * 32;
+        const int cl = (lane & 7) * 4;  // this lane's four columns of the chunk
+        if (d.epi == 2) {  // the product, into M (whole padded tiles)
           float* dstb = d.M + leaf * d.strideM + row0 * d.ldm + col0;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int r = j * 4 + (lane >> 3), c = (lane & 7) * 4;
-            *reinterpret_cast<float4*>(dstb + r * d.ldm + c) = *reinterpret_cast<const float4*>(sb + r * kStageLd + c);
+            const int r = j * 4 + (lane >> 3);
+            *reinterpret_cast<float4*>(dstb + r * d.ldm + cl) = *reinterpret_cast<const float4*>(sb + r * kStageLd + cl);
           }
-          __syncwarp();  // the block is read before the next chunk overwrites it
-          continue;
-        }
-        if (row >= d.m) continue;
-        if (d.epi == 1) {
-          float* dst = d.C + row * d.ldc + col0;
+        } else if (d.epi == 1) {  // L = 0: the product is C (valid rows and columns only)
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (col0 + q < d.m) dst[q] = v[q];
-          continue;
-        }
-        for (int di = 0; di < dl.total; ++di) {
-          int64_t I, J;
-          const float coef = dest_at(dl, di, t.n0, t.L, &I, &J);
-          float* dst = d.C + (I * d.m + row) * d.ldc + J * d.m + col0;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int64_t c = col0 + 4 * q;
-            if (d.vec_ok && c + 3 < d.m) {
-              ptx::red_add_v4(dst + 4 * q, coef * v[4 * q], coef * v[4 * q + 1], coef * v[4 * q + 2],
-                              coef * v[4 * q + 3]);
+          for (int j = 0; j < 8; ++j) {
+            const int r = j * 4 + (lane >> 3);
+            const int64_t gr = row0 + r, gc = col0 + cl;
+            if (gr >= d.m) continue;
+            const float4 x = *reinterpret_cast<const float4*>(sb + r * kStageLd + cl);
+            float* dst = d.C + gr * d.ldc + gc;
+            if (d.vec_ok && gc + 3 < d.m) {
+              *reinterpret_cast<float4*>(dst) = x;
             } else {
+              const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
               for (int e = 0; e < 4; ++e)
-                if (c + e < d.m) atomicAdd(dst + 4 * q + e, coef * v[4 * q + e]);
+                if (gc + e < d.m) dst[e] = xs[e];
+            }
+          }
+        } else {  // fused decode: coef * product added into every C block the leaf feeds
+          for (int di = 0; di < dl.total; ++di) {
+            int64_t I, J;
+            const float coef = dest_at(dl, di, t.n0, t.L, &I, &J);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int r = j * 4 + (lane >> 3);
+              const int64_t gr = row0 + r, gc = col0 + cl;
+              if (gr >= d.m) continue;
+              const float4 x = *reinterpret_cast<const float4*>(sb + r * kStageLd + cl);
+              float* dst = d.C + (I * d.m + gr) * d.ldc + J * d.m + gc;
+              if (d.vec_ok && gc + 3 < d.m) {
+                ptx::red_add_v4(dst, coef * x.x, coef * x.y, coef * x.z, coef * x.w);
+              } else {
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  if (gc + e < d.m) atomicAdd(dst + e, coef * xs[e]);
+              }
             }
           }
         }
+        __syncwarp();  // the block is read before the next chunk overwrites it
       }
       if (++buf == 2) {
         buf = 0;
