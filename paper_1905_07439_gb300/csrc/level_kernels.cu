@@ -1,12 +1,13 @@
-// Encode and decode passes of the recursion (Section 2.1.1, Eq. recursive-random-formula),
-// each pass covering G consecutive levels (G <= 3 for n0 = 2, G <= 2 for n0 = 3, G = 1 for
-// n0 = 4) so that the intermediate operands of those levels never leave registers.
+// Encode and decode passes of the recursion (Section 2.1.1, Eq. recursive-random-formula).
+// Each pass covers G consecutive levels (G <= 2 for n0 = 2, G = 1 for n0 >= 3, see
+// max_levels_per_pass), so that the intermediate operands of those levels never leave
+// registers.
 //
-// At the start of every parent, the CTA expands the randomized tables of the parent's
-// G-level subtree (Prop. 10: u^_klr = u_{pi1(k) pi2(l) r} s1(k) s2(l), likewise v^, w^) from
-// the base tensors and the nodes' packed draws, both held in the constant bank, into shared
-// memory.  The randomization therefore moves no operand data, and the inner loops read each
-// coefficient with one broadcast shared load.
+// Table-driven passes (any formula): at the start of every parent, the CTA expands the
+// randomized tables of the parent's G-level subtree into shared memory (Prop. 10:
+// u^_klr = u_{pi1(k) pi2(l) r} s1(k) s2(l), likewise v^, w^), from the base tensors and the
+// nodes' packed draws, both held in the constant bank.  The randomization therefore moves no
+// operand data, and the inner loops read each coefficient row with 16-byte broadcast loads.
 //
 // Encode pass: a thread owns VEC adjacent positions (y, x..x+VEC-1) of the output blocks. It
 // reads the n0^G x n0^G entries of its parent at those positions, then walks the subtree
@@ -15,8 +16,15 @@
 //
 // Decode pass: the same walk in post-order.  A node's output block (i, j) is
 // sum_r w^(node)_{ijr} M_r (r sequential), M_r the child's output at these positions; the
-// children of a bottom node are loaded eight at a time so that their loads overlap.
+// children of a bottom node are loaded several at a time so that their loads overlap.
 //
+// One-level passes of the built-in formulas (formulas.h) have the formula's sparsity compiled
+// in and apply the node's signed permutation to the operands (encode_fixed_kernel,
+// decode_fixed_kernel); one-level fp32 decodes of other n0 >= 3 formulas use nonzero lists
+// (decode_sparse_kernel).
+//
+// Intermediates use the padded column layout of level_kernels.cuh with zero padding, so the
+// passes that read them take the branch-free vector variant (FAST) whatever m is.
 // Neighbouring threads own neighbouring positions: every load and store is coalesced.
 #include <cuda_runtime.h>
 
