@@ -25,16 +25,37 @@ __device__ __forceinline__ void load_vec(T (&dst)[E], const T* src) {
   }
 }
 
+template <typename T, int E>
+__device__ __forceinline__ void store_vec(T* dst, const T (&x)[E]) {
+  if constexpr (E * sizeof(T) == 16) {
+    int4 v;
+    memcpy(&v, x, 16);
+    *reinterpret_cast<int4*>(dst) = v;
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) dst[e] = x[e];
+  }
+}
+
+// Micro-tile of a thread: TM rows and TN columns of the CTA tile, taken as two halves of
+// contiguous rows (columns), one in each half of the tile, so that each half is read from
+// shared memory (and written out) as one vector.
+template <int H, int HALF>
+__device__ __forceinline__ int micro_index(int t, int i) {
+  return i < H ? t * H + i : HALF + t * H + (i - H);
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     simt_gemm_kernel(const __grid_constant__ Tables<T> t, const SimtGemmArgs a) {
   constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
+  constexpr int HM = TM / 2, HN = TN / 2;  // contiguous rows / columns per half
   constexpr int EA = BM * BK / NT, EB = BN * BK / NT;
   static_assert(BK % EA == 0 && BN % EB == 0 && (BN / EB) * BK == NT, "tile/thread mismatch");
   constexpr int KA = BK / EA;   // threads per row of the S tile (BM rows x BK)
   constexpr int KB = BN / EB;   // threads per row of the T tile (BK rows x BN)
-  __shared__ T As[2][BK][BM];
-  __shared__ T Bs[2][BK][BN];
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN];
   __shared__ DestList<T> dl;
 
   const int tid = threadIdx.x;
@@ -71,10 +92,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         T av[TM], bv[TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i) av[i] = As[buf][kk][ty + i * TY];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx + j * TX];
+        load_vec<T, HM>(*reinterpret_cast<T(*)[HM]>(av), &As[buf][kk][ty * HM]);
+        load_vec<T, HM>(*reinterpret_cast<T(*)[HM]>(av + HM), &As[buf][kk][BM / 2 + ty * HM]);
+        load_vec<T, HN>(*reinterpret_cast<T(*)[HN]>(bv), &Bs[buf][kk][tx * HN]);
+        load_vec<T, HN>(*reinterpret_cast<T(*)[HN]>(bv + HN), &Bs[buf][kk][BN / 2 + tx * HN]);
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -92,17 +113,23 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     if (a.mode == 0) {
       T* M = static_cast<T*>(a.out) + leaf * a.strideO;
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+      for (int i = 0; i < TM; ++i) {
+        T* row = M + (row0 + micro_index<HM, BM / 2>(ty, i)) * a.ldo + col0;
 #pragma unroll
-        for (int j = 0; j < TN; ++j)
-          M[(row0 + ty + i * TY) * a.ldo + col0 + tx + j * TX] = acc[i][j];
+        for (int h = 0; h < 2; ++h) {
+          T part[HN];
+#pragma unroll
+          for (int j = 0; j < HN; ++j) part[j] = acc[i][h * HN + j];
+          store_vec<T, HN>(row + micro_index<HN, BN / 2>(tx, h * HN), part);
+        }
+      }
     } else if (a.mode == 2) {
       T* C = static_cast<T*>(a.out);
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          const int64_t r = row0 + ty + i * TY, c = col0 + tx + j * TX;
+          const int64_t r = row0 + micro_index<HM, BM / 2>(ty, i), c = col0 + micro_index<HN, BN / 2>(tx, j);
           if (r < a.m && c < a.m) C[r * a.ldo + c] = acc[i][j];
         }
     } else {
@@ -116,7 +143,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
-            const int64_t r = row0 + ty + i * TY, c = col0 + tx + j * TX;
+            const int64_t r = row0 + micro_index<HM, BM / 2>(ty, i), c = col0 + micro_index<HN, BN / 2>(tx, j);
             if (r < a.m && c < a.m) atomicAdd(C + (I * a.m + r) * a.ldo + J * a.m + c, coef * acc[i][j]);
           }
       }
@@ -220,9 +247,11 @@ cudaError_t launch_tile(const Tables<T>& t, const SimtGemmArgs& a, cudaStream_t 
 
 }  // namespace
 
+// The large tile wherever it pads m to no more than the small tile plus 1/8.
 int simt_tile(int io, int64_t m) {
-  if (io == RBC_IO_F32) return m >= 256 ? 128 : 32;
-  return m >= 128 ? 64 : 32;
+  const int64_t big = io == RBC_IO_F32 ? 128 : 64;
+  const int64_t pb = (m + big - 1) / big * big, ps = (m + 31) / 32 * 32;
+  return m >= big && pb * 8 <= ps * 9 ? (int)big : 32;
 }
 
 int64_t simt_small_pad(int io, int64_t m) {
