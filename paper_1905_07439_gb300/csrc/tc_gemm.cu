@@ -16,7 +16,9 @@
 //              * M_tile, by 16-byte vector reductions into the zeroed C (or plain stores when
 //              L = 0 / stored M).
 // Split-compensated modes keep hi and lo panels of each operand in a stage and issue
-// hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator.
+// hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator.  Tiles are 256 wide whenever
+// the padded leaf size allows it (a stage then holds 48 KB per panel set: four stages plain,
+// two split), else 128 wide (six stages plain, three split).
 // Every mbarrier wait is bounded (2 s); on expiry the kernel records RBC_ETIMEOUT in the
 // workspace status word, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -441,13 +443,19 @@ cudaError_t dispatch(int leaf, int bn, const CUtensorMap& ma, const CUtensorMap&
                      const Params& p, cudaStream_t st) {
   const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
   const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;
-  if (split && bn != 128) return cudaErrorInvalidValue;
+  // split tiles of width 256 hold two panel pairs per stage (96 KB): two stages fit
   if (tf32) {
-    if (split) return launch<1, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+    if (split) {
+      if (bn == 256) return launch<1, 1, 256, 2, GROUPED>(ma, mb, t, p, st);
+      return launch<1, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+    }
     if (bn == 256) return launch<1, 0, 256, 4, GROUPED>(ma, mb, t, p, st);
     return launch<1, 0, 128, 6, GROUPED>(ma, mb, t, p, st);
   }
-  if (split) return launch<0, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+  if (split) {
+    if (bn == 256) return launch<0, 1, 256, 2, GROUPED>(ma, mb, t, p, st);
+    return launch<0, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+  }
   if (bn == 256) return launch<0, 0, 256, 4, GROUPED>(ma, mb, t, p, st);
   return launch<0, 0, 128, 6, GROUPED>(ma, mb, t, p, st);
 }
@@ -463,8 +471,8 @@ uint32_t leaf_idesc(int leaf, int bn) {
 int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
 
 int tc_default_bn(int leaf, int64_t mp) {
-  const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;
-  return (!split && mp % 256 == 0) ? 256 : 128;
+  (void)leaf;
+  return mp % 256 == 0 ? 256 : 128;
 }
 
 int tc_default_group(int leaf, int64_t mp, int64_t K) {
