@@ -249,11 +249,13 @@ typedef struct {
 typedef struct rbc_group_s* rbc_group_t;
 
 /* Tile configuration chosen by rbc_group_tune: tile width bn (128 or 256), tile order group
- * (0: per-instance default, 1: row-major, 8: groups of 8 tile rows), candidates timed and the
- * best grouped-launch time in milliseconds. */
+ * (0: per-instance default, 1: row-major, 8: groups of 8 tile rows), candidates timed, the
+ * best grouped-launch time in milliseconds, and CTAs per SM (1; or 2, which plain, not split,
+ * leaf modes may take with 128-wide tiles of two pipeline stages each). */
 typedef struct {
   int bn, group, candidates;
   float best_ms;
+  int ctas_per_sm;
 } rbc_group_tuning;
 
 #define RBC_GROUP_GRAPH 1  /* rbc_group_run flag: capture once into a CUDA graph, then replay */
@@ -273,6 +275,13 @@ rbc_status rbc_group_run(rbc_group_t group, void* workspace, size_t workspace_by
  * Synchronizes the stream.  `out` may be NULL. */
 rbc_status rbc_group_tune(rbc_group_t group, void* workspace, size_t workspace_bytes, void* stream,
                           rbc_group_tuning* out);
+/* Apply a tile configuration: bn, group and ctas_per_sm of `cfg` (its other fields are
+ * ignored), e.g. one that rbc_group_tune chose in an earlier process.  The next
+ * rbc_group_run rebinds the instance descriptors (and recaptures its graph).  RBC_EINVAL for
+ * a NULL argument or a configuration the group does not admit: bn 256 needs every padded leaf
+ * size to be a multiple of 256; group must be 0, 1, 2, 4, 8 or 16; ctas_per_sm 2 needs bn 128
+ * and a plain (not split) leaf mode. */
+rbc_status rbc_group_configure(rbc_group_t group, const rbc_group_tuning* cfg);
 void rbc_group_destroy(rbc_group_t group);
 
 /* Serving queue: independent products submitted as they arrive and served with continuous

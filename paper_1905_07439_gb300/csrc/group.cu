@@ -3,8 +3,10 @@
 // leaf products of all instances run in ONE persistent tcgen05 launch whose tile scheduler
 // walks a global tile list (instance-major, then leaf, then tile), reading each instance's
 // descriptor and TMA tensor maps from device memory.  The whole sequence can be captured
-// once into a CUDA graph and replayed; a small autotuner times the candidate tile widths and
-// tile orders of the grouped launch and keeps the fastest for the batch's signature.
+// once into a CUDA graph and replayed; a small autotuner times the candidate tile widths, tile
+// orders and CTAs per SM of the grouped launch and keeps the fastest for the batch's
+// signature.  Every configuration computes each tile with the same instruction sequence, so
+// the configuration changes the speed, not the results.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -28,6 +30,7 @@ namespace {
 struct Config {
   int bn = 128;
   int group = 0;  // 0: per instance default, 1: row-major, 8: groups of 8 tile rows
+  int ctas = 1;   // CTAs per SM of the grouped launch (2: plain 128-wide tiles, two stages each)
 };
 
 std::mutex g_cache_mutex;
@@ -121,6 +124,7 @@ rbc_status grouped_gemm(rbc_group_s* g, char* ws, cudaStream_t st) {
   ga.total_tiles = g->total_tiles;
   ga.leaf = g->leaf;
   ga.bn = g->bound_cfg.bn;
+  ga.ctas = g->bound_cfg.ctas;
   ga.status = reinterpret_cast<int*>(ws);
   cudaError_t e = launch_tc_gemm_grouped(ga, st);
   ++g_launches;
@@ -211,7 +215,7 @@ rbc_status rbc_group_create(const rbc_group_item* items, int count, int leaf_dty
   g->leaf = leaf_dtype;
   g->items.assign(items, items + count);
   size_t off = kStatusBytes;
-  bool all256 = leaf_dtype != RBC_LEAF_3XBF16 && leaf_dtype != RBC_LEAF_3XTF32;
+  bool all256 = true;  // 256-wide tiles: every instance's padded leaf size divisible by 256
   std::ostringstream sig;
   sig << leaf_dtype;
   for (int i = 0; i < count; ++i) {
@@ -252,7 +256,8 @@ rbc_status rbc_group_run(rbc_group_t g, void* workspace, size_t bytes, void* str
   if (s != RBC_OK) return s;
   char* ws = static_cast<char*>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (g->bound_ws != ws || g->bound_cfg.bn != g->cfg.bn || g->bound_cfg.group != g->cfg.group) {
+  if (g->bound_ws != ws || g->bound_cfg.bn != g->cfg.bn || g->bound_cfg.group != g->cfg.group ||
+      g->bound_cfg.ctas != g->cfg.ctas) {
     s = bind(g, ws, g->cfg);
     if (s != RBC_OK) return s;
     if (g->exec) {
@@ -307,9 +312,13 @@ rbc_status rbc_group_tune(rbc_group_t g, void* workspace, size_t bytes, void* st
   if (s == RBC_OK) s = enqueue(g, ws, st);
   if (s != RBC_OK) return s;
   std::vector<Config> cands;
+  const bool split = g->leaf == RBC_LEAF_3XBF16 || g->leaf == RBC_LEAF_3XTF32;
   for (int bn : {128, 256}) {
     if (bn == 256 && !g->bn256_ok) continue;
-    for (int grp : {0, 1, 8}) cands.push_back(Config{bn, grp});
+    for (int ctas : {1, 2}) {
+      if (ctas == 2 && (split || bn != 128)) continue;
+      for (int grp : {0, 1, 8}) cands.push_back(Config{bn, grp, ctas});
+    }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -358,10 +367,26 @@ rbc_status rbc_group_tune(rbc_group_t g, void* workspace, size_t bytes, void* st
   if (out) {
     out->bn = best.bn;
     out->group = best.group;
+    out->ctas_per_sm = best.ctas;
     out->candidates = ntried;
     out->best_ms = best_ms;
   }
   return s;
+}
+
+rbc_status rbc_group_configure(rbc_group_t g, const rbc_group_tuning* cfg) {
+  if (!g || !cfg) return fail(RBC_EINVAL, "null argument");
+  const bool split = g->leaf == RBC_LEAF_3XBF16 || g->leaf == RBC_LEAF_3XTF32;
+  if (cfg->bn != 128 && cfg->bn != 256) return fail(RBC_EINVAL, "bn must be 128 or 256");
+  if (cfg->bn == 256 && !g->bn256_ok) return fail(RBC_EINVAL, "bn 256 needs padded leaf sizes divisible by 256");
+  const int grp = cfg->group;
+  if (grp != 0 && grp != 1 && grp != 2 && grp != 4 && grp != 8 && grp != 16)
+    return fail(RBC_EINVAL, "group must be 0, 1, 2, 4, 8 or 16");
+  if (cfg->ctas_per_sm != 1 && cfg->ctas_per_sm != 2) return fail(RBC_EINVAL, "ctas_per_sm must be 1 or 2");
+  if (cfg->ctas_per_sm == 2 && (split || cfg->bn != 128))
+    return fail(RBC_EINVAL, "two CTAs per SM need bn 128 and a plain leaf mode");
+  g->cfg = Config{cfg->bn, grp, cfg->ctas_per_sm};
+  return RBC_OK;
 }
 
 void rbc_group_destroy(rbc_group_t g) { delete g; }

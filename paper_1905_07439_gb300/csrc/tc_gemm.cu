@@ -103,8 +103,16 @@ __device__ __forceinline__ void tile_coords(int64_t tile, const TcInst& p, int64
   *tn = w / gm;
 }
 
+// Plain 128-wide tiles with two stages (about 84 KB of shared memory, 256 TMEM columns) run
+// two CTAs per SM: small grouped leaves, whose tiles have few K blocks and a full-tile
+// epilogue, then overlap one CTA's epilogue stores with the other's loads and MMAs.  Every
+// other configuration needs more than half of the SM's shared memory, so no other CTA of
+// this kernel can share an SM with a pair, and TMEM (512 columns) always suffices.
+template <int SPLIT, int BN, int STAGES>
+constexpr bool kTwoPerSm = !SPLIT && BN == 128 && STAGES == 2;
+
 template <int KIND, int SPLIT, int BN, int STAGES, bool GROUPED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ Tables<float> t, const Params p) {
   constexpr int P = SPLIT ? 2 : 1;
@@ -414,6 +422,7 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<fl
   constexpr size_t smem =
       (size_t)STAGES * P * (BM + BN) * kRowBytes + ((sizeof(Aux<STAGES>) + 15) & ~(size_t)15) + kStageBytes + 1024;
   static_assert(smem <= 232448, "shared memory budget");
+  static_assert(!kTwoPerSm<SPLIT, BN, STAGES> || 2 * (smem + 1024) <= 233472, "two CTAs per SM");
   auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES, GROUPED>;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -431,18 +440,23 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<fl
     }
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t grid = p.total_tiles < sms ? p.total_tiles : sms;
+  const int64_t cap = (kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1) * (int64_t)sms;
+  const int64_t grid = p.total_tiles < cap ? p.total_tiles : cap;
   if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(ma, mb, t, p);
   return cudaGetLastError();
 }
 
-// Kernel variant for a leaf mode and tile width.
+// Kernel variant for a leaf mode, tile width and CTAs per SM (2: plain 128-wide tiles only).
 template <bool GROUPED>
-cudaError_t dispatch(int leaf, int bn, const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t,
-                     const Params& p, cudaStream_t st) {
+cudaError_t dispatch(int leaf, int bn, int ctas, const CUtensorMap& ma, const CUtensorMap& mb,
+                     const Tables<float>& t, const Params& p, cudaStream_t st) {
   const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
   const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;
+  if (ctas != 1) {
+    if (ctas != 2 || split || bn != 128) return cudaErrorInvalidValue;
+    return tf32 ? launch<1, 0, 128, 2, GROUPED>(ma, mb, t, p, st) : launch<0, 0, 128, 2, GROUPED>(ma, mb, t, p, st);
+  }
   // split tiles of width 256 hold two panel pairs per stage (96 KB): two stages fit
   if (tf32) {
     if (split) {
@@ -529,7 +543,7 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   p.total_tiles = tc_instance_tiles(p.one);
   p.idesc = leaf_idesc(a.leaf, bn);
   p.status = a.status;
-  return dispatch<false>(a.leaf, bn, maps[0], maps[1], t, p, st);
+  return dispatch<false>(a.leaf, bn, 1, maps[0], maps[1], t, p, st);
 }
 
 cudaError_t launch_tc_gemm_grouped(const TcGroupArgs& g, cudaStream_t st) {
@@ -542,7 +556,7 @@ cudaError_t launch_tc_gemm_grouped(const TcGroupArgs& g, cudaStream_t st) {
   p.idesc = leaf_idesc(g.leaf, g.bn);
   p.status = g.status;
   CUtensorMap unused{};
-  return dispatch<true>(g.leaf, g.bn, unused, unused, kNoTables, p, st);
+  return dispatch<true>(g.leaf, g.bn, g.ctas, unused, unused, kNoTables, p, st);
 }
 
 }  // namespace rbc

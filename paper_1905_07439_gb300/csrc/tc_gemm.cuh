@@ -47,6 +47,7 @@ struct TcGroupArgs {
   int64_t total_tiles;
   int leaf;
   int bn;
+  int ctas;  // CTAs per SM: 1, or 2 for plain (not split) 128-wide tiles
   int* status;
 };
 

@@ -43,7 +43,8 @@ class rbc_group_item(C.Structure):
 
 
 class rbc_group_tuning(C.Structure):
-    _fields_ = [("bn", C.c_int), ("group", C.c_int), ("candidates", C.c_int), ("best_ms", C.c_float)]
+    _fields_ = [("bn", C.c_int), ("group", C.c_int), ("candidates", C.c_int), ("best_ms", C.c_float),
+                ("ctas_per_sm", C.c_int)]
 
 
 RBC_GROUP_GRAPH = 1
@@ -86,6 +87,7 @@ SIGNATURES = {
     "rbc_group_workspace_size": (C.c_size_t, [_P]),
     "rbc_group_run": (C.c_int, [_P, _P, C.c_size_t, _P, C.c_int]),
     "rbc_group_tune": (C.c_int, [_P, _P, C.c_size_t, _P, C.POINTER(rbc_group_tuning)]),
+    "rbc_group_configure": (C.c_int, [_P, C.POINTER(rbc_group_tuning)]),
     "rbc_group_destroy": (None, [_P]),
     "rbc_queue_create": (C.c_int, [C.c_int, C.c_size_t, C.c_int, C.POINTER(_P)]),
     "rbc_batch_submit": (C.c_int, [_P, C.POINTER(rbc_request), C.c_int, C.POINTER(C.c_uint64)]),
@@ -346,7 +348,13 @@ class Group:
         t = rbc_group_tuning()
         check(lib().rbc_group_tune(self.handle, workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
                                    C.byref(t)), "rbc_group_tune")
-        return {"bn": t.bn, "group": t.group, "candidates": t.candidates, "best_ms": t.best_ms}
+        return {"bn": t.bn, "group": t.group, "candidates": t.candidates, "best_ms": t.best_ms,
+                "ctas_per_sm": t.ctas_per_sm}
+
+    def configure(self, bn: int = 128, group: int = 0, ctas_per_sm: int = 1) -> None:
+        """Apply a tile configuration (rbc_group_configure)."""
+        t = rbc_group_tuning(bn=bn, group=group, candidates=0, best_ms=0.0, ctas_per_sm=ctas_per_sm)
+        check(lib().rbc_group_configure(self.handle, C.byref(t)), "rbc_group_configure")
 
 
 class Queue:

@@ -118,10 +118,29 @@ def test_workspace_sizes(rbc):
     # staged decode adds the 49 leaf products
     assert fused >= 4 * 2 * 49 * 1024**2
     assert staged - fused >= 4 * 49 * 1024**2
-    # four levels of Strassen run as passes of 1 and 3 levels: one intermediate level
+    # four levels of Strassen run as two passes of two levels: one intermediate level (49
+    # blocks of 2048^2 fp32 per operand) and the bf16 leaves; beyond them only the 256-byte
+    # status word and alignment
     p4 = rbc.Plan(U, V, W, levels=4)
     ws4 = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
-    assert ws4 >= 2 * 4 * 7 * 4096**2 + 2 * 2 * 2401 * 512**2
+    body = 2 * 4 * 49 * 2048**2 + 2 * 2 * 2401 * 512**2
+    assert body <= ws4 <= body + 4096
+
+
+def test_empty_and_ragged_sizes_are_refused(rbc):
+    """N must be a positive multiple of n0^L (the recursion splits N into n0^L equal blocks);
+    an empty product and a ragged N are refused with RBC_EINVAL before any device memory is
+    touched, and need no workspace."""
+    U, V, W = strassen()
+    p = rbc.Plan(U, V, W, levels=2)
+    for n in (0, -4, 6):
+        assert p.workspace_size(n, rbc.IO_F32, rbc.LEAF_BF16) == 0
+    L = rbc.lib()
+    fake = C.c_void_p(1 << 20)   # never dereferenced: the size check comes first
+    for n in (0, -4, 6):
+        st = L.rbc_matmul(p.handle, fake, fake, fake, n, max(n, 1), max(n, 1), max(n, 1),
+                          rbc.IO_F32, rbc.LEAF_BF16, None, 0, None)
+        assert st == 1, (n, st)
 
 
 def test_builtin_formulas_are_recognised(rbc):

@@ -91,3 +91,31 @@ def test_hard_inputs_sampled_parity(rbc):
     B = torch.tensor(Bh, dtype=torch.float32)
     _, n0, rel = _sampled_normwise(rbc, "strassen", n, L, 77, A, B, "3xbf16")
     assert rel <= gate("3xbf16", n0, L, n) * np.sqrt(n), rel   # = t g^L relative to ||AB||
+
+
+@pytest.mark.parametrize("n,L,decode", [(46400, 1, 2), (46400, 1, 1), (47104, 2, 2)])
+def test_more_than_2_31_elements(rbc, n, L, decode):
+    """n^2 > 2^31: element offsets into A, B, C and the workspace need 64 bits, in the passes,
+    the leaf epilogue (staged, decode 2, and fused into C, decode 1) and the decode.  Exact
+    Strassen with bf16 leaves; the RBC of an exact formula equals AB up to rounding (Section 2,
+    orthogonality of the signed permutations), so sampled entries, the last row and column
+    among them, are compared with fp64 dot products of the same rows and columns under the
+    bf16 gate."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(n + L)
+    A = torch.randn((n, n), generator=g, device="cuda")
+    B = torch.randn((n, n), generator=g, device="cuda")
+    plan = rbc.Plan(*formula_by_name("strassen"), levels=L, seed=2024 + L)
+    C = rbc.matmul(plan, A, B, leaf=rbc.LEAF_BF16, decode=decode)
+    rng = np.random.default_rng(n + L)
+    rows, cols = rng.integers(0, n, SAMPLES), rng.integers(0, n, SAMPLES)
+    rows[0], cols[0] = n - 1, n - 1
+    rt, ct = torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")
+    got = C[rt, ct].double().cpu().numpy()
+    want = np.einsum("sk,ks->s", A[rt].double().cpu().numpy(), B[:, ct].double().cpu().numpy())
+    nA = float(np.sqrt(rbc.norms(A).cpu().numpy()[0]))
+    nB = float(np.sqrt(rbc.norms(B).cpu().numpy()[0]))
+    del A, B, C
+    torch.cuda.empty_cache()
+    err = n * np.sqrt(np.mean((got - want) ** 2)) / (nA * nB)
+    assert err <= gate("bf16", 2, L, n), (n, L, decode, err)

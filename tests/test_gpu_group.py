@@ -80,7 +80,9 @@ def test_graph_replay_and_tuning_keep_results(rbc):
     for a, b in zip(eager, Cs):
         assert torch.equal(a, b)
     t = grp.tune(ws)
-    assert t["candidates"] == 6 and t["bn"] in (128, 256) and t["best_ms"] > 0
+    # bn 128 with one or two CTAs per SM and bn 256 with one, each in three tile orders
+    assert t["candidates"] == 9 and t["bn"] in (128, 256) and t["best_ms"] > 0
+    assert t["ctas_per_sm"] in (1, 2) and (t["ctas_per_sm"] == 1 or t["bn"] == 128)
     for c in Cs:
         c.fill_(float("nan"))
     grp.run(ws, graph=True)
@@ -88,3 +90,51 @@ def test_graph_replay_and_tuning_keep_results(rbc):
     for i, (a, b) in enumerate(zip(eager, Cs)):
         A, B = As[i].double().cpu().numpy(), Bs[i].double().cpu().numpy()
         assert normwise(b.double().cpu().numpy(), a.double().cpu().numpy(), A, B) <= 1e-7
+
+
+CONFIGS = [(128, 0, 1), (128, 1, 2), (128, 8, 2), (128, 16, 1), (256, 2, 1)]
+
+
+@pytest.mark.parametrize("leaf", ["bf16", "tf32"])
+@pytest.mark.parametrize("specs", [ALIGNED, RAGGED], ids=["aligned", "ragged"])
+def test_every_configuration_gives_the_same_products(rbc, specs, leaf):
+    """Tile width, tile order and CTAs per SM (rbc_group_configure) change the speed only:
+    each tile runs the same instruction sequence, so for one tile width every configuration
+    gives bit-identical products; the two tile widths agree to rounding."""
+    plans, As, Bs, Cs = _batch(rbc, specs, seed=7)
+    grp = rbc.Group(plans, As, Bs, Cs, rbc.LEAF_NAMES[leaf])
+    ws = torch.empty(grp.workspace_size(), dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    first = {}
+    for bn, group, ctas in CONFIGS:
+        if bn == 256 and specs is RAGGED:
+            with pytest.raises(rbc.RbcError) as e:
+                grp.configure(bn, group, ctas)
+            assert e.value.status == 1
+            continue
+        grp.configure(bn, group, ctas)
+        for c in Cs:
+            c.fill_(float("nan"))
+        grp.run(ws, stream=side, graph=(ctas == 2))
+        torch.cuda.synchronize()
+        got = [c.clone() for c in Cs]
+        if bn not in first:
+            first[bn] = got
+        for i, (a, b) in enumerate(zip(first[bn], got)):
+            assert torch.equal(a, b), (bn, group, ctas, i)
+    if 256 in first:
+        for i, (a, b) in enumerate(zip(first[128], first[256])):
+            A, B = As[i].double().cpu().numpy(), Bs[i].double().cpu().numpy()
+            assert normwise(b.double().cpu().numpy(), a.double().cpu().numpy(), A, B) <= 1e-7, i
+
+
+def test_configuration_arguments(rbc):
+    plans, As, Bs, Cs = _batch(rbc, ALIGNED[:2], seed=9)
+    split = rbc.Group(plans, As, Bs, Cs, rbc.LEAF_3XBF16)
+    for bn, group, ctas in [(64, 0, 1), (128, 3, 1), (128, 0, 3), (256, 0, 2)]:
+        with pytest.raises(rbc.RbcError) as e:
+            split.configure(bn, group, ctas)
+        assert e.value.status == 1, (bn, group, ctas)
+    with pytest.raises(rbc.RbcError):
+        split.configure(128, 0, 2)        # two CTAs per SM: plain leaf modes only
+    split.configure(256, 8, 1)
