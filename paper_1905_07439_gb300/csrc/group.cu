@@ -88,6 +88,7 @@ TcGemmArgs inst_args(const rbc_group_s* g, size_t i, char* ws) {
   a.direct = g->items[i].plan->L == 0;
   a.store_m = g->items[i].plan->L > 0;
   a.M = w + lo.M;
+  a.strideM = lo.mstride;
   a.leaf = g->leaf;
   a.status = reinterpret_cast<int*>(ws);
   return a;

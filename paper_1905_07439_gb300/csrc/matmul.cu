@@ -128,9 +128,10 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   off += leaf_bytes;
   lo->leafT = off;
   off += leaf_bytes;
+  lo->mstride = lo->mp * lo->mp;
   if (lo->decode == 2 && L > 0) {
     lo->M = off;
-    off += align256((size_t)leaves * lo->mp * lo->mp * lo->es_acc);
+    off += align256((size_t)leaves * lo->mstride * lo->es_acc);
     for (int i = 1; i < lo->passes.count; ++i) {
       const int d = lo->passes.top[i];
       const int64_t nd = lo->m * ipow(n0, L - d), wd = lo->seg * ipow(n0, L - d);
@@ -336,9 +337,9 @@ rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc
       a.formula = p->builtin;
       const int64_t first = k0 * P + c0;
       if (bottom) {  // leaf products: rows of mp >= seg columns
-        a.X = ws + lo.M + (size_t)first * outs * lo.mp * lo.mp * lo.es_acc;
+        a.X = ws + lo.M + (size_t)first * outs * lo.mstride * lo.es_acc;
         a.ldx = lo.mp;
-        a.strideX = lo.mp * lo.mp;
+        a.strideX = lo.mstride;
       } else {
         a.X = ws + lo.dec[d + g] + (size_t)first * outs * nb * w_nb * lo.es_acc;
         a.ldx = w_nb;
@@ -412,6 +413,7 @@ rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, 
     g.direct = L == 0;
     g.store_m = !fused;
     g.M = fused ? nullptr : ws + lo.M;
+    g.strideM = lo.mstride;
     g.leaf = leaf;
     g.status = reinterpret_cast<int*>(ws);
     if constexpr (sizeof(T) == 4) {
@@ -440,7 +442,7 @@ rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, 
     } else {
       g.out = ws + lo.M;
       g.ldo = lo.mp;
-      g.strideO = lo.mp * lo.mp;
+      g.strideO = lo.mstride;
       g.mode = 0;
     }
     cudaError_t e = launch_simt_gemm(tab, g, st);

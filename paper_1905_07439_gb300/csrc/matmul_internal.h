@@ -37,6 +37,7 @@ struct Layout {
   Passes passes;
   size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
   size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
+  int64_t mstride = 0;  // elements from one leaf product to the next in M (mp^2)
   size_t total = 0;
 };
 

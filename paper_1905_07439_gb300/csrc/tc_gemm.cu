@@ -528,7 +528,7 @@ bool tc_prepare_instance(const TcGemmArgs& a, int bn, int group_m, int64_t tile_
   x.ldc = a.ldc;
   x.M = static_cast<float*>(a.M);
   x.ldm = a.mp;
-  x.strideM = a.mp * a.mp;
+  x.strideM = a.strideM;
   *d = x;
   return true;
 }

@@ -19,7 +19,8 @@ struct TcGemmArgs {
   int64_t ldc;
   int direct;      // 1: one leaf, plain stores (L = 0)
   int store_m;     // 1: store each leaf product to M (level-by-level decode follows)
-  void* M;         // [leaf][mp][mp] fp32 when store_m
+  void* M;         // [leaf][mp][mp] fp32 when store_m, leaf products strideM elements apart
+  int64_t strideM;
   int leaf;        // rbc_leaf_dtype
   int* status;     // device status word (RBC_ETIMEOUT on an expired wait)
 };
