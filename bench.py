@@ -167,6 +167,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+LEAF_TRAFFIC_3XBF16_STEP = 33_811_097_600
+
+
 def case_flops(n, L, R, n0):
     m = n // n0**L
     return 2.0 * n**3, 2.0 * R**L * m**3
@@ -259,6 +262,7 @@ def run_ours(args):
     # Leaf-product kernel (with fused decode): the dominant kernel.
     leaf_ms, leaf_flops, enc_ms, enc_bytes = 0.0, 0.0, 0.0, 0.0
     per_case, case_model = [], []
+    leaf_bytes = 0.0
     es_leaf = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2}[args.leaf]
     split = 3 if args.leaf.startswith("3x") else 1      # MMA passes per leaf product
     panels = 2 if args.leaf.startswith("3x") else 1     # stored operand panels (hi, lo)
@@ -273,6 +277,8 @@ def run_ours(args):
         lf = split * 2.0 * R**L * m**3
         leaf_ms += g
         leaf_flops += lf
+        # algorithmic leaf bytes: read both operands (all panels), write the fp32 products
+        leaf_bytes += (2 * es_leaf * panels + 4) * R**L * m * m
         # algorithmic encode bytes: read A, B once, write the leaf operands once
         eb = 2 * 4 * n * n + 2 * es_leaf * panels * R**L * m * m
         enc_ms += e
@@ -298,11 +304,18 @@ def run_ours(args):
             "bound": bound, "achieved": round(achieved, 2),
             "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": None,
-            "traffic_note": "per-launch DRAM bytes differ per case; the ncu capture of one launch is summarized "
-                            "in profiles/tc_gemm_3xbf16_leaves.md",
+            "algorithmic_bytes": round(leaf_bytes),
             "peak_source": peak_note,
             "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
                        "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}}
+    if args.leaf == "3xbf16" and len(cases) == len(CASES) and args.decode == 0:
+        # DRAM bytes (read + write) of the step's ten leaf launches, summed, from one ncu capture
+        # of tc_gemm_kernel<0, 1, 256, 2, 0> (profiles/tc_gemm_3xbf16_leaves.md); they exceed the
+        # algorithmic bytes by the tile padding (Laderman 243 -> 256, 729 -> 768, 2187 -> 2304)
+        # and by operand re-reads of the 4096-wide Strassen L = 1 leaves only.
+        roof["traffic"] = LEAF_TRAFFIC_3XBF16_STEP
+        roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the step's 10 leaf "
+                                "launches (one capture, profiles/tc_gemm_3xbf16_leaves.md); compare algorithmic_bytes")
     # Whole-call model: leaf flops at the peak beside the algorithmic bytes (read A, B; write and
     # read the leaf operands; write and read M; write C) at the measured HBM bandwidth.
     t_sum = sum(f / (peak * 1e12) + b / (pk["hbm_gbs"] * 1e9) for f, b, _ in case_model) * 1e3
