@@ -34,6 +34,8 @@ CASES = [("strassen", 8192, L) for L in (1, 2, 3, 4)] + \
         [("laderman", 6561, L) for L in (1, 2, 3)] + \
         [("noisy-strassen", 4096, L) for L in (1, 2, 3)]
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x fp32 lanes x 2 flop x max clock
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates (PFLOP/s): tf32 / bf16
+NOMINAL_HBM_GBS = 8000.0     # nominal HBM3e bandwidth, beside the measured copy figure
 
 
 def parse():
@@ -50,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--decode", type=int, default=0, help="0 auto, 1 fused, 2 staged")
     ap.add_argument("--no-errors", action="store_true", help="skip the error pass after the timing")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "experiments", "precision"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "experiments", "precision", "peaks"],
                     help="sweep: the at-scale fp32 sweep (default); batch: 512 uneven instances in one "
                          "grouped leaf launch replayed from a CUDA graph")
     ap.add_argument("--instances", type=int, default=512)
@@ -294,10 +296,10 @@ def run_ours(args):
         bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
         peak_note = "fp32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"
     else:
-        ratio = 0.5 if args.leaf in ("tf32", "3xtf32") else 1.0
+        ratio = TF32_PER_BF16 if args.leaf in ("tf32", "3xtf32") else 1.0
         bound, unit = "tensor", "TFLOP/s"
         peak = pk["bf16_tflops_sustained"] * ratio
-        peak_note = f"{pk_kind} bf16 sustained x {ratio} (nominal {args.leaf}/bf16 ratio)"
+        peak_note = f"{pk_kind} bf16 sustained x {ratio:.4f} (nominal {args.leaf}/bf16 ratio)"
     achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
     roof = {"kernel": "tc_gemm_kernel / simt_gemm_kernel: the leaf products of all cases of the step "
                       "(achieved = their algorithmic flops / their summed event time)",
@@ -307,7 +309,8 @@ def run_ours(args):
             "algorithmic_bytes": round(leaf_bytes),
             "peak_source": peak_note,
             "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
-                       "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}}
+                       "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                       "frac_of_nominal_8000": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}}
     if args.leaf == "3xbf16" and len(cases) == len(CASES) and args.decode == 0:
         # DRAM bytes (read + write) of the step's ten leaf launches, summed, from one ncu capture
         # of tc_gemm_kernel<0, 1, 256, 2, 0> (profiles/tc_gemm_3xbf16_leaves.md); they exceed the
@@ -1067,8 +1070,60 @@ def run_serve(args):
         print(json.dumps(line))
 
 
+def run_peaks(args):
+    """cuBLAS GEMM throughput per dtype on this GPU (torch.matmul of n x n operands, n^3
+    multiply-adds): a measured context for the leaf modes whose roofline peaks are derived
+    (fp32 FMA from unit counts and clock, tf32 and f16 from the measured bf16 peak and the
+    nominal rate ratios).  Each dtype: a burst of about 0.3 s, then a loop of about 3 s
+    (sustained).  One JSON line; not a step of the method."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    res = {}
+    cases = [("f32", torch.float32, False, 8192), ("tf32", torch.float32, True, 8192),
+             ("f16", torch.float16, False, 8192), ("bf16", torch.bfloat16, False, 8192),
+             ("f64", torch.float64, False, 4096)]
+    prev = torch.backends.cuda.matmul.allow_tf32
+    with ClockSampler(0) as clk:
+        for name, dtype, tf32, n in cases:
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            g = torch.Generator(device=dev)
+            g.manual_seed(n)
+            a = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32).to(dtype)
+            b = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32).to(dtype)
+            c = torch.empty((n, n), device=dev, dtype=dtype)
+            for _ in range(3):
+                torch.matmul(a, b, out=c)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            one = max(e0.elapsed_time(e1), 1e-3)
+            out = {}
+            for label, secs in (("burst", 0.3), ("sustained", 3.0)):
+                reps = max(3, int(secs * 1e3 / one))
+                e0.record()
+                for _ in range(reps):
+                    torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                out[label] = round(2.0 * n**3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12, 1)
+            out["n"] = n
+            res[name] = out
+            del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    print(json.dumps({"metric": "cuBLAS GEMM TFLOP/s per dtype (torch.matmul)", "unit": "TFLOP/s", "n_gpus": 1,
+                      "peaks": res, "derived_fp32_fma_tflops": round(FP32_PEAK_TFLOPS, 1),
+                      "nominal_tf32_per_bf16": round(TF32_PER_BF16, 4), "clocks": clk.summary()}))
+
+
 def main():
     args = parse()
+    if args.workload == "peaks":
+        run_peaks(args)
+        return
     if args.workload == "serve" and args.impl != "reference":
         run_serve(args)
         return
