@@ -392,14 +392,17 @@ def run_ours(args):
         barrier()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         a0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             e2e_step()
+            marks[k].record(stream)
         a1.record(stream)
         barrier()
         e_ms = a0.elapsed_time(a1) / args.steps
+        step_ms = [round((a0 if k == 0 else marks[k - 1]).elapsed_time(marks[k]), 3) for k in range(args.steps)]
         e2e = {"value": round(world * eff_flops / (e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
-               "ms_per_step": round(e_ms, 3),
+               "ms_per_step": round(e_ms, 3), "step_ms": step_ms,
                "h2d_bytes_per_step": sum(2 * 4 * n * n for n in sorted({c[1] for c in cases})),
                "d2h_bytes_per_step": sum(4 * n * n for _, n, _ in cases)}
 
