@@ -161,7 +161,13 @@ rbc_status rbc_matmul(rbc_plan_t plan, const void* A, const void* B, void* C, in
  * so its summation order, and the last bits of C, may vary from call to call. */
 typedef struct {
   int decode;
-  int reserved[7];
+  /* Test hook for the bounded-wait path (0 = off; tensor-core leaf modes only, else
+   * RBC_EINVAL): the leaf kernel issues no operand copies, so the first wait of its MMA warp
+   * expires after 2 s; the kernel then records RBC_ETIMEOUT in the workspace status word (read
+   * by rbc_workspace_check), releases its tensor memory and returns without the product.
+   * Nothing faults and the CUDA context stays usable. */
+  int stall_leaf_copies;
+  int reserved[6];
   /* Optional timing hooks: CUDA events (cudaEvent_t as void*, NULL = skip) recorded on the
    * call's stream at [0] the start, [1] the end of the encode, [2] the end of the leaf
    * products (including a fused decode), [3] the end of the call. */

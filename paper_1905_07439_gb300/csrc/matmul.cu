@@ -416,6 +416,7 @@ rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, 
     g.strideM = lo.mstride;
     g.leaf = leaf;
     g.status = reinterpret_cast<int*>(ws);
+    g.stall = opts ? opts->stall_leaf_copies : 0;
     if constexpr (sizeof(T) == 4) {
       cudaError_t e = launch_tc_gemm(tab, g, st);
       ++g_launches;
@@ -486,6 +487,8 @@ rbc_status rbc_matmul_ex(rbc_plan_t plan, const void* A, const void* B, void* C,
                          size_t ws_bytes, void* stream, rbc_matmul_opts* opts) {
   if (!plan || !A || !B || !C) return fail(RBC_EINVAL, "null argument");
   if (opts && (opts->decode < 0 || opts->decode > 2)) return fail(RBC_EINVAL, "bad decode option");
+  if (opts && opts->stall_leaf_copies && !is_tc_leaf(leaf))
+    return fail(RBC_EINVAL, "the stall test hook applies to tensor-core leaf modes");
   Layout lo;
   rbc_status s = make_layout(plan, N, io, leaf, opts ? opts->decode : 0, &lo);
   if (s != RBC_OK) return s;

@@ -51,6 +51,7 @@ struct Params {
   int64_t total_tiles;
   uint32_t idesc;
   int* status;
+  int stall;  // test hook: the producer issues no copies, so the MMA warp's first wait expires
 };
 
 // Instance owning global tile `tile`: the last one whose tile_begin <= tile.
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
       uint32_t ph = 0;
       uint32_t armed = 0, last_par = 0;  // per-stage bit masks for the teardown drain
       int fenced = -1;                   // grouped: instance whose maps were last fenced
-      for (int64_t tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
+      for (int64_t tile = blockIdx.x; tile < p.total_tiles && !*abort && !p.stall; tile += gridDim.x) {
         const int ii = find_inst<GROUPED>(p, tile);
         const TcInst d = GROUPED ? p.insts[ii] : p.one;
         const void* mA = GROUPED ? (const void*)&p.maps[2 * ii] : (const void*)&tmA;
@@ -549,6 +550,7 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   p.total_tiles = tc_instance_tiles(p.one);
   p.idesc = leaf_idesc(a.leaf, bn);
   p.status = a.status;
+  p.stall = a.stall;
   return dispatch<false>(a.leaf, bn, pair ? 2 : 1, maps[0], maps[1], t, p, st);
 }
 

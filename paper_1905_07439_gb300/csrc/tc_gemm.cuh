@@ -23,6 +23,7 @@ struct TcGemmArgs {
   int64_t strideM;
   int leaf;        // rbc_leaf_dtype
   int* status;     // device status word (RBC_ETIMEOUT on an expired wait)
+  int stall;       // test hook: issue no operand copies (the bounded waits then expire)
 };
 
 // One instance of a (possibly grouped) leaf-product launch, as the kernel reads it.

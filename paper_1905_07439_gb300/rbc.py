@@ -63,7 +63,8 @@ class rbc_queue_info(C.Structure):
 
 
 class rbc_matmul_opts(C.Structure):
-    _fields_ = [("decode", C.c_int), ("reserved", C.c_int * 7), ("events", C.c_void_p * 4),
+    _fields_ = [("decode", C.c_int), ("stall_leaf_copies", C.c_int), ("reserved", C.c_int * 6),
+                ("events", C.c_void_p * 4),
                 ("launches", C.c_int64)]
 
 
@@ -212,7 +213,7 @@ def _stream_ptr(stream):
 
 
 def matmul(plan: Plan, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, stream=None,
-           decode: int = 0, events=None):
+           decode: int = 0, events=None, stall_leaf_copies: int = 0):
     """C = F^(L)(A, B) through rbc_matmul_ex on torch CUDA tensors (row-major, unit column stride)."""
     import torch
     N = A.shape[0]
@@ -231,7 +232,7 @@ def matmul(plan: Plan, A, B, C_out=None, leaf: int = LEAF_F32, workspace=None, s
         pass
     if workspace is None:
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
-    o = rbc_matmul_opts(decode)
+    o = rbc_matmul_opts(decode, stall_leaf_copies)
     if events is not None:
         for i, ev in enumerate(events):
             o.events[i] = ev.cuda_event if ev is not None else None

@@ -200,3 +200,46 @@ def test_workspace_status_word_clear_after_calls(rbc):
     st = ctypes.c_int(-1)
     rbc.rbc.check(rbc.lib().rbc_workspace_check(ws.data_ptr(), None, ctypes.byref(st)), "check")
     assert st.value == 0
+
+
+@pytest.mark.parametrize("leaf,decode", [("bf16", 2), ("3xbf16", 2), ("bf16", 1)])
+def test_expired_wait_reports_timeout_and_the_context_survives(rbc, leaf, decode):
+    """Failure detection without a fault.  With the stall test hook the leaf kernel issues no
+    operand copies, so its MMA warp's bounded wait (2 s) expires: the kernel records
+    RBC_ETIMEOUT in the workspace status word, releases its tensor memory and returns, and
+    rbc_workspace_check reports it.  The next call on the same context and workspace is
+    correct (the check cleared the word)."""
+    import ctypes
+    import time
+    U, V, W = formula("strassen")
+    N = 512
+    plan = rbc.Plan(U, V, W, levels=1, seed=11)
+    A, B = matrix_pair("normal", N, seed=12)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    At = torch.tensor(A, dtype=torch.float32, device="cuda")
+    Bt = torch.tensor(B, dtype=torch.float32, device="cuda")
+    lf = rbc.LEAF_NAMES[leaf]
+    ws = torch.empty(plan.workspace_size(N, rbc.IO_F32, lf, decode), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    st = ctypes.c_int(-1)
+    t0 = time.monotonic()
+    rbc.matmul(plan, At, Bt, leaf=lf, workspace=ws, decode=decode, stall_leaf_copies=1)
+    status = rbc.lib().rbc_workspace_check(ws.data_ptr(), None, ctypes.byref(st))
+    waited = time.monotonic() - t0
+    assert status == rbc.RBC_ETIMEOUT and st.value == rbc.RBC_ETIMEOUT, (status, st.value)
+    assert 1.5 < waited < 60, waited
+    C = rbc.matmul(plan, At, Bt, leaf=lf, workspace=ws, decode=decode)
+    status = rbc.lib().rbc_workspace_check(ws.data_ptr(), None, ctypes.byref(st))
+    assert status == rbc.RBC_OK and st.value == 0
+    ref = o.rbc(A, B, oracle_plan(U, V, W, 1, 11))
+    assert normwise(C.double().cpu().numpy(), ref, A, B) <= gate(leaf, 2, 1, N)
+
+
+def test_stall_hook_needs_a_tensor_core_leaf_mode(rbc):
+    U, V, W = formula("strassen")
+    plan = rbc.Plan(U, V, W, levels=1, seed=11)
+    A = torch.zeros((256, 256), device="cuda")
+    with pytest.raises(rbc.RbcError) as e:
+        rbc.matmul(plan, A, A, leaf=rbc.LEAF_F32, stall_leaf_copies=1)
+    assert e.value.status == rbc.RBC_EINVAL
