@@ -155,3 +155,59 @@ def test_builtin_formulas_are_recognised(rbc):
     W = W.copy()
     W[0, 0, 0] = 2.0  # one coefficient changed: generic
     assert rbc.Plan(U, V, W, levels=1).info()["builtin_formula"] == 0
+
+
+def _fake_group(rbc, specs, leaf):
+    """A group over fake device pointers: creation computes layouts and the tile-width
+    eligibility on the host and touches no memory."""
+    from paper_1905_07439_gb300.rbc import rbc_group_item
+    plans = [rbc.Plan(*fn(), levels=L, seed=1) for fn, L, _ in specs]
+    items = (rbc_group_item * len(specs))()
+    for i, (p, (_, _, N)) in enumerate(zip(plans, specs)):
+        fake = C.c_void_p(1 << 30)
+        items[i] = rbc_group_item(p.handle, fake, fake, fake, N, N, N, N)
+    h = C.c_void_p()
+    assert rbc.lib().rbc_group_create(items, len(specs), leaf, C.byref(h)) == 0
+    return h, plans
+
+
+def test_group_configuration_validation(rbc):
+    """rbc_group_configure admits bn 128 always and bn 256 only when every padded leaf size is
+    a multiple of 256; group orders 0, 1, 2, 4, 8, 16; two CTAs per SM only for plain leaf
+    modes with bn 128.  Checked on the host (no launch)."""
+    from paper_1905_07439_gb300.rbc import rbc_group_tuning
+    L = rbc.lib()
+    aligned = [(strassen, 1, 512), (strassen, 2, 1024), (laderman, 1, 768)]   # m = 256 each
+    ragged = [(strassen, 1, 512), (strassen, 1, 2 * 320)]                       # m = 320 pads to 384
+    cases = [
+        (aligned, rbc.LEAF_BF16, [(128, 0, 1), (128, 8, 2), (256, 16, 1), (128, 2, 2)],
+         [(64, 0, 1), (128, 3, 1), (128, 0, 3), (256, 0, 2)]),
+        (aligned, rbc.LEAF_3XBF16, [(128, 1, 1), (256, 4, 1)], [(128, 0, 2), (256, 8, 2)]),
+        (ragged, rbc.LEAF_TF32, [(128, 8, 1), (128, 0, 2)], [(256, 0, 1), (256, 8, 2)]),
+    ]
+    for specs, leaf, good, bad in cases:
+        h, plans = _fake_group(rbc, specs, leaf)
+        try:
+            for bn, grp, ctas in good:
+                t = rbc_group_tuning(bn=bn, group=grp, candidates=0, best_ms=0.0, ctas_per_sm=ctas)
+                assert L.rbc_group_configure(h, C.byref(t)) == 0, (leaf, bn, grp, ctas)
+            for bn, grp, ctas in bad:
+                t = rbc_group_tuning(bn=bn, group=grp, candidates=0, best_ms=0.0, ctas_per_sm=ctas)
+                assert L.rbc_group_configure(h, C.byref(t)) == 1, (leaf, bn, grp, ctas)
+            assert L.rbc_group_configure(h, None) == 1
+        finally:
+            L.rbc_group_destroy(h)
+
+
+def test_stall_hook_is_refused_for_simt_leaves(rbc):
+    """The stall test hook applies to the tensor-core leaf kernel only; with a CUDA-core leaf
+    mode rbc_matmul_ex refuses it before any device work."""
+    from paper_1905_07439_gb300.rbc import rbc_matmul_opts
+    p = rbc.Plan(*strassen(), levels=1, seed=1)
+    fake = C.c_void_p(1 << 20)
+    for leaf in (rbc.LEAF_F32, rbc.LEAF_F64):
+        io = rbc.IO_F64 if leaf == rbc.LEAF_F64 else rbc.IO_F32
+        o = rbc_matmul_opts(2, 1)
+        st = rbc.lib().rbc_matmul_ex(p.handle, fake, fake, fake, 256, 256, 256, 256, io, leaf,
+                                     fake, 1 << 30, None, C.byref(o))
+        assert st == 1, (leaf, st)
