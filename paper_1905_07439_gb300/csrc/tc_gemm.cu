@@ -425,6 +425,9 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<fl
       (size_t)STAGES * P * (BM + BN) * kRowBytes + ((sizeof(Aux<STAGES>) + 15) & ~(size_t)15) + kStageBytes + 1024;
   static_assert(smem <= 232448, "shared memory budget");
   static_assert(!kTwoPerSm<SPLIT, BN, STAGES> || 2 * (smem + 1024) <= 233472, "two CTAs per SM");
+  // a CTA of any other configuration takes more than half of the SM's shared memory, so it never
+  // shares an SM (and its TMEM) with another CTA of this kernel
+  static_assert(kTwoPerSm<SPLIT, BN, STAGES> || 2 * (smem + 1024) > 233472, "one CTA per SM");
   auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES, GROUPED>;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
