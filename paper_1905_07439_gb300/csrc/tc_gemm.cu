@@ -2,7 +2,8 @@
 // 5th-generation tensor cores, batched over all R^L leaves, with the decode of
 // Eq. recursive-random-formula fused into the epilogue.
 //
-// Persistent, warp-specialized kernel, one CTA per SM (192 threads):
+// Persistent, warp-specialized kernel, one CTA per SM (192 threads; two per SM for small
+// plain leaves, see kTwoPerSm):
 //   warp 0     one thread issues TMA loads of the S tile (K-major) and the T tile (MN-major:
 //              T is stored row-major with n contiguous) with the 128-byte swizzle into a ring
 //              of shared-memory stages (mbarrier full/empty handshake);
