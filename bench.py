@@ -12,6 +12,11 @@ host-to-device copies of A, B and the device-to-host copy of C inside the timed 
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
 same workload.  Multi-GPU: the path does not shard (no collectives): N replicas.
+
+Other workloads (--workload): precision (Strassen N = 16384, every leaf mode), batch (512
+uneven instances in one grouped launch), serve (10,000 Poisson requests through the queue),
+experiments (the Section 3 error experiments), peaks (cuBLAS GEMM throughput per dtype, as
+context for the derived roofline peaks).
 """
 from __future__ import annotations
 
