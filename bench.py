@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--leaf", default="3xbf16",
-                    help="leaf mode; default 3xbf16: fp32 I/O with compensated bf16 leaves, the fastest "
-                         "mode within the fp32 tolerance (relative error <= 2e-5 * g^L)")
+    ap.add_argument("--leaf", default=None,
+                    help="leaf mode; default for the sweep bf16x6: fp32 I/O with six-product bf16 tensor-core "
+                         "leaves, as accurate as fp32 arithmetic (3xbf16, bf16, ... are the precision sweep); "
+                         "default for the batch workload bf16")
     ap.add_argument("--cases", default="all", help="'all' or comma list of indices into the sweep")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -174,7 +175,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-LEAF_TRAFFIC_3XBF16_STEP = 33_811_097_600
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the step's ten leaf launches,
+# summed over one ncu capture of the full sweep, keyed by (leaf mode, library version): a
+# capture describes the kernel it measured only, so another library version reports null.
+LEAF_TRAFFIC_STEP = {}
+# Stored panels per leaf operand and tensor-core products per leaf product of each leaf mode.
+LEAF_PANELS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 2, "3xtf32": 2, "bf16x6": 3}
+LEAF_PRODUCTS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 3, "3xtf32": 3, "bf16x6": 6}
+LEAF_BYTES = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2, "bf16x6": 2}
 
 
 def case_flops(n, L, R, n0):
@@ -270,9 +278,9 @@ def run_ours(args):
     leaf_ms, leaf_flops, enc_ms, enc_bytes = 0.0, 0.0, 0.0, 0.0
     per_case, case_model = [], []
     leaf_bytes = 0.0
-    es_leaf = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2}[args.leaf]
-    split = 3 if args.leaf.startswith("3x") else 1      # MMA passes per leaf product
-    panels = 2 if args.leaf.startswith("3x") else 1     # stored operand panels (hi, lo)
+    es_leaf = LEAF_BYTES[args.leaf]
+    split = LEAF_PRODUCTS[args.leaf]   # MMA passes per leaf product
+    panels = LEAF_PANELS[args.leaf]    # stored operand panels
     for i, (nm, n, L) in enumerate(cases):
         U = formula_by_name(nm, 7)[0]
         R, n0 = U.shape[2], U.shape[0]
@@ -301,29 +309,31 @@ def run_ours(args):
         bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
         peak_note = "fp32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"
     else:
+        # the leaf launches last about a millisecond each (their event times are summed), so the
+        # burst figure is the ceiling; the sustained one is reported beside it
         ratio = TF32_PER_BF16 if args.leaf in ("tf32", "3xtf32") else 1.0
         bound, unit = "tensor", "TFLOP/s"
-        peak = pk["bf16_tflops_sustained"] * ratio
-        peak_note = f"{pk_kind} bf16 sustained x {ratio:.4f} (nominal {args.leaf}/bf16 ratio)"
+        peak = pk["bf16_tflops"] * ratio
+        peak_note = (f"{pk_kind} bf16 burst x {ratio:.4f} (nominal {args.leaf}/bf16 ratio); achieved counts "
+                     f"{split} tensor-core products per leaf product")
     achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
     roof = {"kernel": "tc_gemm_kernel / simt_gemm_kernel: the leaf products of all cases of the step "
                       "(achieved = their algorithmic flops / their summed event time)",
             "bound": bound, "achieved": round(achieved, 2),
             "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
+            "frac_of_sustained": (round(achieved / (pk["bf16_tflops_sustained"] * ratio), 4)
+                                  if bound == "tensor" else None),
             "traffic": None,
             "algorithmic_bytes": round(leaf_bytes),
             "peak_source": peak_note,
             "encode": {"achieved_gbs": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1),
                        "peak_gbs": pk["hbm_gbs"], "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
                        "frac_of_nominal_8000": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4)}}
-    if args.leaf == "3xbf16" and len(cases) == len(CASES) and args.decode == 0:
-        # DRAM bytes (read + write) of the step's ten leaf launches, summed, from one ncu capture
-        # of tc_gemm_kernel<0, 1, 256, 2, 0> (profiles/tc_gemm_3xbf16_leaves.md); they exceed the
-        # algorithmic bytes by the tile padding (Laderman 243 -> 256, 729 -> 768, 2187 -> 2304)
-        # and by operand re-reads of the 4096-wide Strassen L = 1 leaves only.
-        roof["traffic"] = LEAF_TRAFFIC_3XBF16_STEP
+    key = (args.leaf, int(rbc.lib().rbc_version()))
+    if key in LEAF_TRAFFIC_STEP and len(cases) == len(CASES) and args.decode == 0:
+        roof["traffic"] = LEAF_TRAFFIC_STEP[key]
         roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the step's 10 leaf "
-                                "launches (one capture, profiles/tc_gemm_3xbf16_leaves.md); compare algorithmic_bytes")
+                                f"launches (one capture of library version {key[1]}); compare algorithmic_bytes")
     # Whole-call model: leaf flops at the peak beside the algorithmic bytes (read A, B; write and
     # read the leaf operands; write and read M; write C) at the measured HBM bandwidth.
     t_sum = sum(f / (peak * 1e12) + b / (pk["hbm_gbs"] * 1e9) for f, b, _ in case_model) * 1e3
@@ -563,7 +573,7 @@ def run_reference(args):
         return
     per = []
     for _ in range(args.warmup):
-        pass
+        cpu_baseline(budget_s=0.0)  # untimed: the same product as a timed step
     t0 = time.perf_counter()
     res = None
     for _ in range(args.steps):
@@ -611,7 +621,7 @@ def run_batch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     init_dist(world, dev)
-    leaf_name = args.leaf if args.leaf != "3xbf16" else "bf16"  # the batched workload runs bf16 leaves
+    leaf_name = args.leaf or "bf16"  # the batched workload runs bf16 leaves
     leaf = rbc.LEAF_NAMES[leaf_name]
     specs = batch_specs(args.instances)
     gen = torch.Generator(device="cuda")
@@ -701,7 +711,7 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
-PRECISION_LEAVES = ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "f32"]
+PRECISION_LEAVES = ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f32"]
 
 
 def run_precision(args):
@@ -946,7 +956,7 @@ def run_experiments(args):
         print(json.dumps(line))
 
 
-SERVE_LEAF = {"fp32": "3xbf16", "bf16-leaf": "bf16", "3xbf16-leaf": "3xbf16"}
+SERVE_LEAF = {"fp32": "bf16x6", "bf16-leaf": "bf16", "3xbf16-leaf": "3xbf16"}
 
 
 def serve_specs(count: int, rate: float, seed: int = 5):
@@ -1059,7 +1069,7 @@ def run_serve(args):
     line = {
         "metric": METRIC, "value": round(len(specs) / span, 2), "unit": "requests/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": round(span * 1e3, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 io; leaves per request (fp32 -> 3xbf16, bf16, 3xbf16)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 io; leaves per request (fp32 -> bf16x6, bf16, 3xbf16)",
         "data": "synthetic (seeded N(0,1); Poisson arrivals)",
         "config": {"workload": f"rbc-serve: {len(specs)} requests, Poisson {args.rate:g}/s, n log-uniform "
                                "[128,8192], strassen/laderman/noisy-strassen, L in {1,2,3} (clamped for small n), "
@@ -1144,6 +1154,7 @@ def main():
     elif args.workload == "precision":
         run_precision(args)
     else:
+        args.leaf = args.leaf or "bf16x6"
         run_ours(args)
 
 

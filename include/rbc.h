@@ -56,7 +56,12 @@ typedef enum { RBC_IO_F64 = 0, RBC_IO_F32 = 1 } rbc_io_dtype;
 
 /* Arithmetic of the leaf products F^(0) (Section 2.1.1).  Encode and decode run in the
  * I/O type; leaves accumulate in fp32 (fp64 for RBC_LEAF_F64).  The split modes store
- * x = hi + lo with hi = round(x), lo = round(x - hi) and compute hi*hi' + hi*lo' + lo*hi'. */
+ * x = hi + lo with hi = round(x), lo = round(x - hi) and compute hi*hi' + hi*lo' + lo*hi'.
+ * RBC_LEAF_BF16X6 stores three bf16 pieces x = b0 + b1 + b2 (b0 = round(x),
+ * b1 = round(x - b0), b2 = round(x - b0 - b1); exact for normal fp32 x) and adds the six
+ * products whose pieces carry the leading 24 bits, b0*b2' + b2*b0' + b1*b1' + b0*b1' +
+ * b1*b0' + b0*b0' (the bf16x6 method of Henry, Tang & Heinecke, 2019): an fp32-accurate
+ * product on the bf16 tensor cores. */
 typedef enum {
   RBC_LEAF_F64 = 0,    /* fp64 FMA (SIMT); I/O must be F64                         */
   RBC_LEAF_F32 = 1,    /* fp32 FMA (SIMT)                                          */
@@ -64,7 +69,8 @@ typedef enum {
   RBC_LEAF_BF16 = 3,   /* tcgen05 kind::f16 with bf16 operands                      */
   RBC_LEAF_F16 = 4,    /* tcgen05 kind::f16 with fp16 operands                      */
   RBC_LEAF_3XBF16 = 5, /* three bf16 tcgen05 products (split compensated)          */
-  RBC_LEAF_3XTF32 = 6  /* three tf32 tcgen05 products (split compensated)          */
+  RBC_LEAF_3XTF32 = 6, /* three tf32 tcgen05 products (split compensated)         */
+  RBC_LEAF_BF16X6 = 7  /* six bf16 tcgen05 products of three-piece splits (fp32 level) */
 } rbc_leaf_dtype;
 
 /* Which parts of the signed permutations are drawn (Section 3.2: fully randomized,

@@ -313,9 +313,9 @@ rbc_status rbc_group_tune(rbc_group_t g, void* workspace, size_t bytes, void* st
   if (s == RBC_OK) s = enqueue(g, ws, st);
   if (s != RBC_OK) return s;
   std::vector<Config> cands;
-  const bool split = g->leaf == RBC_LEAF_3XBF16 || g->leaf == RBC_LEAF_3XTF32;
+  const bool split = leaf_panels(g->leaf) > 1;
   for (int bn : {128, 256}) {
-    if (bn == 256 && !g->bn256_ok) continue;
+    if (bn == 256 && (!g->bn256_ok || g->leaf == RBC_LEAF_BF16X6)) continue;
     for (int ctas : {1, 2}) {
       if (ctas == 2 && (split || bn != 128)) continue;
       for (int grp : {0, 1, 8}) cands.push_back(Config{bn, grp, ctas});
@@ -377,9 +377,10 @@ rbc_status rbc_group_tune(rbc_group_t g, void* workspace, size_t bytes, void* st
 
 rbc_status rbc_group_configure(rbc_group_t g, const rbc_group_tuning* cfg) {
   if (!g || !cfg) return fail(RBC_EINVAL, "null argument");
-  const bool split = g->leaf == RBC_LEAF_3XBF16 || g->leaf == RBC_LEAF_3XTF32;
+  const bool split = leaf_panels(g->leaf) > 1;
   if (cfg->bn != 128 && cfg->bn != 256) return fail(RBC_EINVAL, "bn must be 128 or 256");
   if (cfg->bn == 256 && !g->bn256_ok) return fail(RBC_EINVAL, "bn 256 needs padded leaf sizes divisible by 256");
+  if (cfg->bn == 256 && g->leaf == RBC_LEAF_BF16X6) return fail(RBC_EINVAL, "bf16x6 leaves take bn 128");
   const int grp = cfg->group;
   if (grp != 0 && grp != 1 && grp != 2 && grp != 4 && grp != 8 && grp != 16)
     return fail(RBC_EINVAL, "group must be 0, 1, 2, 4, 8 or 16");

@@ -261,15 +261,31 @@ struct EncodeEmitV {
       memcpy(hi, h2, sizeof(hi));
       store_some<Tout, VEC>(dst, hi, vec, avail);
       if (split) {
+        // remainders x - b0 (and x - b0 - b1) are exact in fp32: each piece keeps the
+        // leading 8 significant bits of what is left
+        float rem[VEC];
         typename P::T l2[VEC / 2];
         Tout lo[VEC];
 #pragma unroll
         for (int i = 0; i < VEC / 2; ++i) {
           const float2 h = P::back(h2[i]);
-          l2[i] = P::cvt(val[2 * i] - h.x, val[2 * i + 1] - h.y);
+          rem[2 * i] = val[2 * i] - h.x;
+          rem[2 * i + 1] = val[2 * i + 1] - h.y;
+          l2[i] = P::cvt(rem[2 * i], rem[2 * i + 1]);
         }
         memcpy(lo, l2, sizeof(lo));
         store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
+        if (split > 1) {
+          typename P::T t2[VEC / 2];
+          Tout lo2[VEC];
+#pragma unroll
+          for (int i = 0; i < VEC / 2; ++i) {
+            const float2 l = P::back(l2[i]);
+            t2[i] = P::cvt(rem[2 * i] - l.x, rem[2 * i + 1] - l.y);
+          }
+          memcpy(lo2, t2, sizeof(lo2));
+          store_some<Tout, VEC>(dst + 2 * kpanel, lo2, vec, avail);
+        }
       }
     } else {
       Tout hi[VEC];
@@ -277,10 +293,19 @@ struct EncodeEmitV {
       for (int v = 0; v < VEC; ++v) hi[v] = to_store<S>((double)val[v]);
       store_some<Tout, VEC>(dst, hi, vec, avail);
       if (split) {
+        Tc rem[VEC];
         Tout lo[VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(val[v] - (Tc)from_store<S>(hi[v])));
+        for (int v = 0; v < VEC; ++v) {
+          rem[v] = val[v] - (Tc)from_store<S>(hi[v]);
+          lo[v] = to_store<S>((double)rem[v]);
+        }
         store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
+        if (split > 1) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(rem[v] - (Tc)from_store<S>(lo[v])));
+          store_some<Tout, VEC>(dst + 2 * kpanel, lo, vec, avail);
+        }
       }
     }
   }
@@ -377,7 +402,12 @@ struct TransposedEmit {
     Tout* dst = Y + path * strideY + (x0 + r) * ldy + (y0 + c);
     const Tout hi = to_store<S>((double)w);
     dst[0] = hi;
-    if (split) dst[kpanel] = to_store<S>((double)(w - (Tc)from_store<S>(hi)));
+    if (split) {
+      const Tc rem = w - (Tc)from_store<S>(hi);
+      const Tout lo = to_store<S>((double)rem);
+      dst[kpanel] = lo;
+      if (split > 1) dst[2 * kpanel] = to_store<S>((double)(rem - (Tc)from_store<S>(lo)));
+    }
     buf ^= 1;
   }
 };
@@ -1020,7 +1050,13 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
   Tout* dst = static_cast<Tout*>(a.Y) + y * a.ldy + x;
   const Tout hi = to_store<S>(v);
   dst[0] = hi;
-  if (a.split) dst[a.kpanel] = to_store<S>(v - from_store<S>(hi));
+  if (a.split) {
+    // v holds an fp32 value: the remainders below are exact
+    const double rem = v - from_store<S>(hi);
+    const Tout lo = to_store<S>(rem);
+    dst[a.kpanel] = lo;
+    if (a.split > 1) dst[2 * a.kpanel] = to_store<S>(rem - from_store<S>(lo));
+  }
 }
 
 }  // namespace

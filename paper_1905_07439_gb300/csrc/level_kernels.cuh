@@ -21,7 +21,7 @@ namespace rbc {
 //           of nb x nb blocks, plain (plain = 1) or recursive with sub-block width xcol;
 //           Y = outputs, output `path` of parent p at Y + (p*outs_per_parent + path)*strideY,
 //           leading dim ldy, rows_out x cols_out physical positions written (padding
-//           positions are zeros), split panels [hi | lo] kpanel apart.  Positions x with
+//           positions are zeros), split panels [hi | lo] (or [b0 | b1 | b2]) kpanel apart.  Positions x with
 //           x % seg >= mval or rows y >= nb are padding.
 //   decode: X = children (child `path` of parent p at X + (p*outs_per_parent + path)*strideX,
 //           leading dim ldx), nb rows x xcol physical columns (padding as above); Y = parents
@@ -50,7 +50,7 @@ struct PassArgs {
   int depth;
   int tensor;     // encode: 0 left operand (u^), 1 right operand (v^)
   int formula;    // rbc::BuiltinFormula of the plan's U, V, W (compiled-in one-level passes)
-  int split;      // encode: write [hi | lo] panels
+  int split;      // encode: extra panels written, 0 none, 1 [hi | lo], 2 [b0 | b1 | b2]
   int trans;      // encode, last pass: write each output transposed
   int vload;      // set by the launcher: input rows allow VEC-wide vector loads
   int vstore;     // set by the launcher: output rows allow VEC-wide vector stores

@@ -22,7 +22,12 @@ thread_local int64_t g_launches = 0;  // kernels launched by the current call
 
 bool is_tc_leaf(int leaf) {
   return leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_BF16 || leaf == RBC_LEAF_F16 ||
-         leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32;
+         leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_BF16X6;
+}
+
+int leaf_panels(int leaf) {
+  if (leaf == RBC_LEAF_BF16X6) return 3;
+  return (leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32) ? 2 : 1;
 }
 
 int leaf_store(int leaf) {
@@ -32,7 +37,8 @@ int leaf_store(int leaf) {
     case RBC_LEAF_TF32:
     case RBC_LEAF_3XTF32: return kStoreTF32;
     case RBC_LEAF_BF16:
-    case RBC_LEAF_3XBF16: return kStoreBF16;
+    case RBC_LEAF_3XBF16:
+    case RBC_LEAF_BF16X6: return kStoreBF16;
     case RBC_LEAF_F16: return kStoreF16;
   }
   return -1;
@@ -71,7 +77,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   if (reals > 1 && (p->L == 0 || decode_req != 2))
     return fail(RBC_EINVAL, "realization batches need L >= 1 and staged decode");
   if (io != RBC_IO_F32 && io != RBC_IO_F64) return fail(RBC_EINVAL, "bad io dtype");
-  if (leaf < RBC_LEAF_F64 || leaf > RBC_LEAF_3XTF32) return fail(RBC_EINVAL, "bad leaf dtype");
+  if (leaf < RBC_LEAF_F64 || leaf > RBC_LEAF_BF16X6) return fail(RBC_EINVAL, "bad leaf dtype");
   if (io == RBC_IO_F64 && leaf != RBC_LEAF_F64)
     return fail(RBC_EUNSUPPORTED, "fp64 I/O supports the fp64 leaf mode only");
   if (io == RBC_IO_F32 && leaf == RBC_LEAF_F64)
@@ -85,7 +91,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   lo->es_acc = lo->es_io;
   lo->store = leaf_store(leaf);
   lo->es_leaf = store_bytes(lo->store);
-  lo->split = (leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32) ? 1 : 0;
+  lo->split = leaf_panels(leaf) - 1;  // extra panels of a split leaf operand
   // Small SIMT leaves take the exact-size product kernel, which stores M (staged decode) or
   // C (L = 0); an explicitly fused decode keeps the tiled kernel.
   const int64_t small = is_tc_leaf(leaf) || (decode_req == 1 && L > 0) ? 0 : simt_small_pad(io, lo->m);
@@ -97,7 +103,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     const int tile = simt_tile(io, lo->m);
     lo->mp = (lo->m + tile - 1) / tile * tile;
   }
-  lo->K = lo->mp * (lo->split ? 2 : 1);
+  lo->K = lo->mp * (1 + lo->split);
   lo->seg = seg_pitch(lo->m);
   lo->passes = plan_passes(L, n0);
   const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;

@@ -32,7 +32,8 @@ struct Passes {
 struct Layout {
   int64_t m = 0, mp = 0, K = 0;
   int64_t seg = 0;  // seg_pitch(m): an intermediate block at depth d is m n0^(L-d) rows x seg n0^(L-d) columns
-  int store = 0, split = 0, decode = 0;  // decode: 1 fused, 2 staged passes
+  int store = 0, decode = 0;  // decode: 1 fused, 2 staged passes
+  int split = 0;              // extra panels of the leaf operands: 0 plain, 1 [hi | lo], 2 [b0 | b1 | b2]
   size_t es_io = 0, es_acc = 0, es_leaf = 0;
   Passes passes;
   size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
@@ -53,6 +54,7 @@ struct Reals {
 };
 
 bool is_tc_leaf(int leaf);
+int leaf_panels(int leaf);  // stored panels per leaf operand: 1, 2 (split modes) or 3 (bf16x6)
 Passes plan_passes(int L, int n0);
 // reals > 1: the layout of that many realizations (staged decode only).
 rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo,

@@ -7,7 +7,8 @@
 //   warp 0     one thread issues TMA loads of the S tile (K-major) and the T tile (MN-major:
 //              T is stored row-major with n contiguous) with the 128-byte swizzle into a ring
 //              of shared-memory stages (mbarrier full/empty handshake);
-//   warp 1     allocates TMEM (two fp32 accumulators of 128 x BN) and one thread issues
+//   warp 1     allocates TMEM (two fp32 accumulators of 128 x BN; for bf16x6 two buffers of a
+//              main and a cross-term accumulator, drained every 256 elements of K) and one thread issues
 //              tcgen05.mma (M = 128, N = BN, K = 16 bf16/f16 or 8 tf32 per instruction),
 //              committing stage releases and accumulator-ready signals;
 //   warps 2-5  drain an accumulator with tcgen05.ld (one TMEM lane = one tile row per
@@ -17,9 +18,11 @@
 //              * M_tile, by 16-byte vector reductions into the zeroed C (or plain stores when
 //              L = 0 / stored M).
 // Split-compensated modes keep hi and lo panels of each operand in a stage and issue
-// hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator.  Tiles are 256 wide whenever
-// the padded leaf size allows it (a stage then holds 48 KB per panel set: four stages plain,
-// two split), else 128 wide (six stages plain, three split).
+// hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator; the bf16x6 mode keeps three
+// panels b0, b1, b2 per operand and issues b0*b2' + b2*b0' + b1*b1' + b0*b1' + b1*b0' +
+// b0*b0' (smallest terms first).  Tiles are 256 wide whenever the padded leaf size allows it
+// (a stage then holds 48 KB per panel set: four stages plain, two split), else 128 wide (six
+// stages plain, three split); bf16x6 tiles are 128 wide with two stages of 96 KB.
 // Every mbarrier wait is bounded (2 s); on expiry the kernel records RBC_ETIMEOUT in the
 // workspace status word, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -111,14 +114,15 @@ __device__ __forceinline__ void tile_coords(int64_t tile, const TcInst& p, int64
 // epilogue, then overlap one CTA's epilogue stores with the other's loads and MMAs.  Every
 // other configuration needs more than half of the SM's shared memory, so no other CTA of
 // this kernel can share an SM with a pair, and TMEM (512 columns) always suffices.
-template <int SPLIT, int BN, int STAGES>
-constexpr bool kTwoPerSm = !SPLIT && BN == 128 && STAGES == 2;
+template <int P, int BN, int STAGES>
+constexpr bool kTwoPerSm = P == 1 && BN == 128 && STAGES == 2;
 
-template <int KIND, int SPLIT, int BN, int STAGES, bool GROUPED>
-__global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1)
+// P: stored panels per operand (1 plain, 2 split [hi | lo], 3 bf16x6 [b0 | b1 | b2]).
+template <int KIND, int P, int BN, int STAGES, bool GROUPED>
+__global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ Tables<float> t, const Params p) {
-  constexpr int P = SPLIT ? 2 : 1;
+  static_assert(P >= 1 && P <= 3 && (P < 3 || KIND == 0), "three panels are bf16 only");
   constexpr uint32_t A_BYTES = BM * kRowBytes, B_BYTES = BN * kRowBytes;
   constexpr uint32_t STAGE_BYTES = P * (A_BYTES + B_BYTES);
   constexpr int KSTEPS = kRowBytes / 32;  // MMA K steps per stage (32 bytes of K in A rows)
@@ -129,6 +133,14 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
   // kind::f16 reads T MN-major (as stored); kind::tf32 takes only K-major operands, so its
   // right operand is stored transposed (T^T, rows n) and loaded like S.
   constexpr bool BMN = KIND == 0;
+  // The tensor cores accumulate in fp32 with truncation, whose error grows with the number of
+  // accumulations into one sum.  bf16x6 tiles therefore accumulate chunks of KCH K blocks
+  // (256 elements of K) in TMEM, each in two accumulators (main term, cross terms), and the
+  // epilogue adds the chunks in fp32 registers with round-to-nearest.  Other modes accumulate
+  // a whole tile in one accumulator.
+  constexpr int KCH = P == 3 ? 4 : (1 << 30);
+  constexpr int ACC_COLS = P == 3 ? 2 * BN : BN;  // TMEM columns of one accumulator buffer
+  static_assert(2 * ACC_COLS <= 512, "two accumulator buffers fit TMEM");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
     }
   }
   if (warp == 1) {
-    ptx::tmem_alloc(&aux->tmem_base, 2 * BN);
+    ptx::tmem_alloc(&aux->tmem_base, 2 * ACC_COLS);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -193,22 +205,22 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
           uint8_t* st = smem + s * STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&aux->full[s], STAGE_BYTES);
           const int32_t kx = kb * KELEM;
-          ptx::tma_load_2d(st, mA, &aux->full[s], kx, rowA);
-          if (SPLIT) ptx::tma_load_2d(st + A_BYTES, mA, &aux->full[s], kx + d.kpanel, rowA);
+#pragma unroll
+          for (int q = 0; q < P; ++q) ptx::tma_load_2d(st + q * A_BYTES, mA, &aux->full[s], kx + q * d.kpanel, rowA);
           if constexpr (BMN) {
             const int32_t rowB = (int32_t)(leaf * d.mp) + kx;
             constexpr int NBOX = kRowBytes / (KIND == 0 ? 2 : 4);
 #pragma unroll
-            for (int j = 0; j < B_BOXES; ++j) {
-              ptx::tma_load_2d(st + P * A_BYTES + j * B_ATOM, mB, &aux->full[s], colB + j * NBOX, rowB);
-              if (SPLIT)
-                ptx::tma_load_2d(st + P * A_BYTES + B_BYTES + j * B_ATOM, mB, &aux->full[s],
-                                 colB + j * NBOX + d.kpanel, rowB);
-            }
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+              for (int j = 0; j < B_BOXES; ++j)
+                ptx::tma_load_2d(st + P * A_BYTES + q * B_BYTES + j * B_ATOM, mB, &aux->full[s],
+                                 colB + j * NBOX + q * d.kpanel, rowB);
           } else {
             const int32_t rowB = (int32_t)(leaf * d.mp) + colB;
-            ptx::tma_load_2d(st + P * A_BYTES, mB, &aux->full[s], kx, rowB);
-            if (SPLIT) ptx::tma_load_2d(st + P * A_BYTES + B_BYTES, mB, &aux->full[s], kx + d.kpanel, rowB);
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+              ptx::tma_load_2d(st + P * A_BYTES + q * B_BYTES, mB, &aux->full[s], kx + q * d.kpanel, rowB);
           }
           armed |= 1u << s;
           last_par = (last_par & ~(1u << s)) | (ph << s);
@@ -231,15 +243,20 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
       int s = 0, buf = 0;
       uint32_t ph = 0, aph = 0;
       for (int64_t tile = blockIdx.x; tile < p.total_tiles && !*abort; tile += gridDim.x) {
-        if (!ptx::wait_bounded(&aux->tempty[buf], aph ^ 1u, abort, kWaitNs)) {
-          raise_abort(abort, p.status);
-          break;
-        }
-        ptx::tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
         const int nk = GROUPED ? p.insts[find_inst<GROUPED>(p, tile)].nk : p.one.nk;
         bool ok = true;
+        uint32_t d_tmem = 0;
         for (int kb = 0; kb < nk; ++kb) {
+          const int kc = kb % KCH;  // K block inside the current accumulator chunk
+          if (kc == 0) {            // a chunk starts: wait for a drained accumulator
+            if (!ptx::wait_bounded(&aux->tempty[buf], aph ^ 1u, abort, kWaitNs)) {
+              raise_abort(abort, p.status);
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            d_tmem = tmem_base + (uint32_t)(buf * ACC_COLS);
+          }
           if (!ptx::wait_bounded(&aux->full[s], ph, abort, kWaitNs)) {
             raise_abort(abort, p.status);
             ok = false;
@@ -250,19 +267,32 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
           const uint32_t b0 = a0 + P * A_BYTES;
 #pragma unroll
           for (int k = 0; k < KSTEPS; ++k) {
-            const uint64_t ahi = ptx::desc_sw128(a0 + k * 32);
-            const uint64_t bhi = BMN ? ptx::desc_sw128_mn(b0 + k * KINSTR * 128, 1024, B_ATOM)
-                                     : ptx::desc_sw128(b0 + k * 32);
-            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-            if (SPLIT) {
-              const uint64_t alo = ptx::desc_sw128(a0 + A_BYTES + k * 32);
-              const uint64_t blo = BMN ? ptx::desc_sw128_mn(b0 + B_BYTES + k * KINSTR * 128, 1024, B_ATOM)
-                                       : ptx::desc_sw128(b0 + B_BYTES + k * 32);
-              ptx::mma<KIND>(d_tmem, ahi, blo, p.idesc, acc);
-              ptx::mma<KIND>(d_tmem, alo, bhi, p.idesc, 1u);
-              ptx::mma<KIND>(d_tmem, ahi, bhi, p.idesc, 1u);
+            // descriptors of panel q of A and B at this K step
+            uint64_t ad[P], bd[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+              ad[q] = ptx::desc_sw128(a0 + q * A_BYTES + k * 32);
+              bd[q] = BMN ? ptx::desc_sw128_mn(b0 + q * B_BYTES + k * KINSTR * 128, 1024, B_ATOM)
+                          : ptx::desc_sw128(b0 + q * B_BYTES + k * 32);
+            }
+            const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+            if constexpr (P == 3) {
+              // five cross terms (at most 2^-8 of the leading one) into their own accumulator,
+              // b0*b0' alone into the main one: only one truncating accumulation of the main
+              // sum per K step
+              const uint32_t d_small = d_tmem + (uint32_t)BN;
+              ptx::mma<KIND>(d_small, ad[0], bd[2], p.idesc, acc);
+              ptx::mma<KIND>(d_small, ad[2], bd[0], p.idesc, 1u);
+              ptx::mma<KIND>(d_small, ad[1], bd[1], p.idesc, 1u);
+              ptx::mma<KIND>(d_small, ad[0], bd[1], p.idesc, 1u);
+              ptx::mma<KIND>(d_small, ad[1], bd[0], p.idesc, 1u);
+              ptx::mma<KIND>(d_tmem, ad[0], bd[0], p.idesc, acc);
+            } else if constexpr (P == 2) {
+              ptx::mma<KIND>(d_tmem, ad[0], bd[1], p.idesc, acc);
+              ptx::mma<KIND>(d_tmem, ad[1], bd[0], p.idesc, 1u);
+              ptx::mma<KIND>(d_tmem, ad[0], bd[0], p.idesc, 1u);
             } else {
-              ptx::mma<KIND>(d_tmem, ahi, bhi, p.idesc, acc);
+              ptx::mma<KIND>(d_tmem, ad[0], bd[0], p.idesc, acc);
             }
           }
           ptx::mma_commit(&aux->empty[s]);  // stage free once these MMAs have read it
@@ -270,13 +300,15 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
             s = 0;
             ph ^= 1u;
           }
+          if (kc == KCH - 1 || kb == nk - 1) {
+            ptx::mma_commit(&aux->tfull[buf]);  // chunk (or tile) accumulated
+            if (++buf == 2) {
+              buf = 0;
+              aph ^= 1u;
+            }
+          }
         }
         if (!ok) break;
-        ptx::mma_commit(&aux->tfull[buf]);  // accumulator complete
-        if (++buf == 2) {
-          buf = 0;
-          aph ^= 1u;
-        }
       }
       // All MMAs issued by this thread complete before TMEM is released.
       ptx::mma_commit(&aux->drain);
@@ -296,29 +328,12 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
       tile_coords(tile - d.tile_begin, d, &leaf, &tm, &tn);
       __syncwarp();  // every lane is done with the previous tile's list
       if (d.epi == 0 && lane == 0) build_dest_list(t, leaf, dl);
-      int ok = 1;
-      if (lane == 0) ok = ptx::wait_bounded(&aux->tfull[buf], aph, abort, kWaitNs) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) raise_abort(abort, p.status);
-        break;
-      }
-      __syncwarp();
-      ptx::tc_fence_after();
-      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        ptx::tmem_ld32(tbase + (uint32_t)c0, v);
-        if (c0 + 32 == BN) {
-          // accumulator fully read: hand it back to the MMA warp before the global writes
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&aux->tempty[buf]);
-        }
+      // Output of one 32-column block v of this warp's 32 rows.  Every output goes through
+      // shared memory, so that each store (or reduction) instruction covers four whole
+      // 128-byte row segments: a lane holds one row of the accumulator, and the 32 x 32 block
+      // is re-read by rows.
+      auto out_block = [&](const float (&v)[32], int c0) {
         const int64_t col0 = (int64_t)tn * BN + c0;
-        // Every output goes through shared memory, so that each store (or reduction)
-        // instruction covers four whole 128-byte row segments: a lane holds one row of the
-        // accumulator, and the 32 x 32 block is re-read by rows.
         float* sb = ostage + (warp - 2) * 32 * kStageLd;
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -373,11 +388,77 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
             }
           }
         }
-        __syncwarp();  // the block is read before the next chunk overwrites it
-      }
-      if (++buf == 2) {
-        buf = 0;
-        aph ^= 1u;
+        __syncwarp();  // the block is read before the next one overwrites it
+      };
+      int ok = 1;
+      if constexpr (P == 3) {
+        // chunks of the tile's K: sum main and cross-term accumulators in registers (fp32,
+        // round to nearest), releasing each accumulator buffer as soon as it is read
+        const int nch = (d.nk + KCH - 1) / KCH;
+        float sum[BN];
+#pragma unroll
+        for (int i = 0; i < BN; ++i) sum[i] = 0.f;
+        for (int c = 0; c < nch; ++c) {
+          if (lane == 0) ok = ptx::wait_bounded(&aux->tfull[buf], aph, abort, kWaitNs) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) break;
+          __syncwarp();
+          ptx::tc_fence_after();
+          const uint32_t tb = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * ACC_COLS);
+#pragma unroll
+          for (int c0 = 0; c0 < BN; c0 += 32) {
+            float x[32];
+            ptx::tmem_ld32(tb + (uint32_t)(BN + c0), x);  // cross terms
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sum[c0 + i] += x[i];
+            ptx::tmem_ld32(tb + (uint32_t)c0, x);         // main term
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sum[c0 + i] += x[i];
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&aux->tempty[buf]);
+          if (++buf == 2) {
+            buf = 0;
+            aph ^= 1u;
+          }
+        }
+        if (!ok) {
+          if (lane == 0) raise_abort(abort, p.status);
+          break;
+        }
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = sum[c0 + i];
+          out_block(v, c0);
+        }
+      } else {
+        if (lane == 0) ok = ptx::wait_bounded(&aux->tfull[buf], aph, abort, kWaitNs) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) raise_abort(abort, p.status);
+          break;
+        }
+        __syncwarp();
+        ptx::tc_fence_after();
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          float v[32];
+          ptx::tmem_ld32(tbase + (uint32_t)c0, v);
+          if (c0 + 32 == BN) {
+            // accumulator fully read: hand it back to the MMA warp before the global writes
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&aux->tempty[buf]);
+          }
+          out_block(v, c0);
+        }
+        if (++buf == 2) {
+          buf = 0;
+          aph ^= 1u;
+        }
       }
     }
   }
@@ -386,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem_base, 2 * BN);
+    ptx::tmem_dealloc(tmem_base, 2 * ACC_COLS);
   }
 }
 
@@ -418,18 +499,17 @@ bool make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int es
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KIND, int SPLIT, int BN, int STAGES, bool GROUPED>
+template <int KIND, int P, int BN, int STAGES, bool GROUPED>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t, const Params& p,
                    cudaStream_t st) {
-  constexpr int P = SPLIT ? 2 : 1;
   constexpr size_t smem =
       (size_t)STAGES * P * (BM + BN) * kRowBytes + ((sizeof(Aux<STAGES>) + 15) & ~(size_t)15) + kStageBytes + 1024;
   static_assert(smem <= 232448, "shared memory budget");
-  static_assert(!kTwoPerSm<SPLIT, BN, STAGES> || 2 * (smem + 1024) <= 233472, "two CTAs per SM");
+  static_assert(!kTwoPerSm<P, BN, STAGES> || 2 * (smem + 1024) <= 233472, "two CTAs per SM");
   // a CTA of any other configuration takes more than half of the SM's shared memory, so it never
   // shares an SM (and its TMEM) with another CTA of this kernel
-  static_assert(kTwoPerSm<SPLIT, BN, STAGES> || 2 * (smem + 1024) > 233472, "one CTA per SM");
-  auto kern = tc_gemm_kernel<KIND, SPLIT, BN, STAGES, GROUPED>;
+  static_assert(kTwoPerSm<P, BN, STAGES> || 2 * (smem + 1024) > 233472, "one CTA per SM");
+  auto kern = tc_gemm_kernel<KIND, P, BN, STAGES, GROUPED>;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   // Once per device (never inside a later stream capture): allow the large shared memory.
@@ -446,7 +526,7 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<fl
     }
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t cap = (kTwoPerSm<SPLIT, BN, STAGES> ? 2 : 1) * (int64_t)sms;
+  const int64_t cap = (kTwoPerSm<P, BN, STAGES> ? 2 : 1) * (int64_t)sms;
   const int64_t grid = p.total_tiles < cap ? p.total_tiles : cap;
   if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(ma, mb, t, p);
@@ -459,25 +539,30 @@ cudaError_t dispatch(int leaf, int bn, int ctas, const CUtensorMap& ma, const CU
                      const Tables<float>& t, const Params& p, cudaStream_t st) {
   const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
   const bool split = leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_3XBF16;
+  if (leaf == RBC_LEAF_BF16X6) {
+    // three 16 KB panels of A and of B per stage: two stages of 96 KB at 128-wide tiles
+    if (ctas != 1 || bn != 128) return cudaErrorInvalidValue;
+    return launch<0, 3, 128, 2, GROUPED>(ma, mb, t, p, st);
+  }
   if (ctas != 1) {
     if (ctas != 2 || split || bn != 128) return cudaErrorInvalidValue;
-    return tf32 ? launch<1, 0, 128, 2, GROUPED>(ma, mb, t, p, st) : launch<0, 0, 128, 2, GROUPED>(ma, mb, t, p, st);
+    return tf32 ? launch<1, 1, 128, 2, GROUPED>(ma, mb, t, p, st) : launch<0, 1, 128, 2, GROUPED>(ma, mb, t, p, st);
   }
   // split tiles of width 256 hold two panel pairs per stage (96 KB): two stages fit
   if (tf32) {
     if (split) {
-      if (bn == 256) return launch<1, 1, 256, 2, GROUPED>(ma, mb, t, p, st);
-      return launch<1, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+      if (bn == 256) return launch<1, 2, 256, 2, GROUPED>(ma, mb, t, p, st);
+      return launch<1, 2, 128, 3, GROUPED>(ma, mb, t, p, st);
     }
-    if (bn == 256) return launch<1, 0, 256, 4, GROUPED>(ma, mb, t, p, st);
-    return launch<1, 0, 128, 6, GROUPED>(ma, mb, t, p, st);
+    if (bn == 256) return launch<1, 1, 256, 4, GROUPED>(ma, mb, t, p, st);
+    return launch<1, 1, 128, 6, GROUPED>(ma, mb, t, p, st);
   }
   if (split) {
-    if (bn == 256) return launch<0, 1, 256, 2, GROUPED>(ma, mb, t, p, st);
-    return launch<0, 1, 128, 3, GROUPED>(ma, mb, t, p, st);
+    if (bn == 256) return launch<0, 2, 256, 2, GROUPED>(ma, mb, t, p, st);
+    return launch<0, 2, 128, 3, GROUPED>(ma, mb, t, p, st);
   }
-  if (bn == 256) return launch<0, 0, 256, 4, GROUPED>(ma, mb, t, p, st);
-  return launch<0, 0, 128, 6, GROUPED>(ma, mb, t, p, st);
+  if (bn == 256) return launch<0, 1, 256, 4, GROUPED>(ma, mb, t, p, st);
+  return launch<0, 1, 128, 6, GROUPED>(ma, mb, t, p, st);
 }
 
 uint32_t leaf_idesc(int leaf, int bn) {
@@ -491,7 +576,7 @@ uint32_t leaf_idesc(int leaf, int bn) {
 int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
 
 int tc_default_bn(int leaf, int64_t mp) {
-  (void)leaf;
+  if (leaf == RBC_LEAF_BF16X6) return 128;  // a 256-wide stage of three panel pairs does not fit twice
   return mp % 256 == 0 ? 256 : 128;
 }
 
@@ -545,7 +630,8 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   // tiles have at most four K blocks, and the second CTA overlaps one CTA's epilogue with the
   // other's loads (bf16 Laderman leaves of 243 -> 256: 1.05 -> 0.92 ms per launch; at 512 the
   // 256-wide single CTA per SM stays faster, 0.76 against 0.93 ms).
-  const bool pair = !(a.leaf == RBC_LEAF_3XBF16 || a.leaf == RBC_LEAF_3XTF32) && a.mp <= 256;
+  const bool pair = !(a.leaf == RBC_LEAF_3XBF16 || a.leaf == RBC_LEAF_3XTF32 || a.leaf == RBC_LEAF_BF16X6) &&
+                    a.mp <= 256;
   const int bn = pair ? 128 : tc_default_bn(a.leaf, a.mp);
   CUtensorMap maps[2];
   Params p{};

@@ -125,6 +125,12 @@ def test_workspace_sizes(rbc):
     ws4 = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
     body = 2 * 4 * 49 * 2048**2 + 2 * 2 * 2401 * 512**2
     assert body <= ws4 <= body + 4096
+    # split leaves store two bf16 panels per operand, bf16x6 three: the leaf operand bytes
+    # grow by one and two panels
+    panel = 2 * 2 * 2401 * 512**2
+    ws4_3x = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_3XBF16, decode=1)
+    ws4_6x = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16X6, decode=1)
+    assert ws4_3x - ws4 == panel and ws4_6x - ws4 == 2 * panel
 
 
 def test_empty_and_ragged_sizes_are_refused(rbc):
@@ -184,6 +190,8 @@ def test_group_configuration_validation(rbc):
          [(64, 0, 1), (128, 3, 1), (128, 0, 3), (256, 0, 2)]),
         (aligned, rbc.LEAF_3XBF16, [(128, 1, 1), (256, 4, 1)], [(128, 0, 2), (256, 8, 2)]),
         (ragged, rbc.LEAF_TF32, [(128, 8, 1), (128, 0, 2)], [(256, 0, 1), (256, 8, 2)]),
+        # three panels per operand: only 128-wide tiles fit two stages
+        (aligned, rbc.LEAF_BF16X6, [(128, 0, 1), (128, 8, 1)], [(256, 0, 1), (128, 0, 2)]),
     ]
     for specs, leaf, good, bad in cases:
         h, plans = _fake_group(rbc, specs, leaf)

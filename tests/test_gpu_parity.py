@@ -159,7 +159,7 @@ TC_CASES = [
 ]
 
 
-@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32"])
+@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6"])
 @pytest.mark.parametrize("decode", [1, 2])
 @pytest.mark.parametrize("name,L,N", TC_CASES)
 def test_tensor_core_leaves_match_oracle(rbc, name, L, N, decode, leaf):
@@ -188,6 +188,44 @@ def test_split_modes_are_fp32_accurate(rbc):
     assert errs["3xtf32"] < errs["tf32"] / 50
     assert errs["3xbf16"] < errs["bf16"] / 50
     assert errs["3xtf32"] < 4 * errs["f32"] + 1e-7
+
+
+BF16X6_CASES = [
+    # formula, L, N, distribution: exact and approximate formulas, n0 = 2 and 3, zero-mean and
+    # entrywise-positive badly scaled inputs, classical (L = 0)
+    ("strassen", 0, 1024, "normal"),
+    ("strassen", 2, 4 * 256, "normal"),
+    ("strassen", 2, 4 * 256, "hard"),
+    ("strassen", 3, 8 * 128, "normal"),
+    ("laderman", 2, 9 * 100, "normal"),
+    ("laderman", 1, 3 * 300, "hard"),
+    ("noisy-strassen", 2, 4 * 260, "normal"),
+]
+
+
+@pytest.mark.parametrize("name,L,N,dist", BF16X6_CASES)
+def test_bf16x6_is_as_accurate_as_fp32_leaves(rbc, name, L, N, dist):
+    """The six-product bf16 mode stores fp32 leaf operands exactly as three bf16 pieces and
+    drops only products below 2^-24 of the leading one, so its distance to the fp64 oracle (same
+    draws) is that of fp32 arithmetic: at most twice the fp32 CUDA-core leaves' distance on the
+    same inputs, and within the fp32 gate."""
+    U, V, W = formula(name, seed=4)
+    A, B = matrix_pair(dist, N, seed=40 + L)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    plan = rbc.Plan(U, V, W, levels=L, seed=808)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, 808))
+    e32 = rel(gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_F32, 2), ref)
+    C6 = gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_BF16X6, 2)
+    e6 = rel(C6, ref)
+    assert e6 <= 2.0 * e32, (e6, e32)
+    if dist == "normal":
+        assert normwise(C6, ref, A, B) <= gate("bf16x6", U.shape[0], L, N)
+        # the three-piece split is exact: against the two-piece split it gains by far where the
+        # leaf products' rounding dominates (zero-mean inputs; on the scaled positive inputs the
+        # fp32 encode of mixed row scales dominates both)
+        e3 = rel(gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_3XBF16, 2), ref)
+        assert e6 < e3 / 4, (e6, e3)
 
 
 def test_workspace_status_word_clear_after_calls(rbc):
