@@ -452,19 +452,6 @@ def expected_one_level(A, B, U, V, W, scale: float, mode: int = RAND_FULL) -> np
     return acc / len(draws)
 
 
-def expected_two_level_per_level(A, B, U, V, W, scale: float) -> np.ndarray:
-    """E[F^(2)(A, B)] with one draw set per level (Section 2.1.1), by averaging
-    over every (outer draw, inner draw) pair; the inner draw is shared by all R
-    inner calls."""
-    draws = all_node_draws(U.shape[0])
-    acc = np.zeros((A.shape[0], A.shape[0]))
-    for d_out in draws:
-        for d_in in draws:
-            inner = lambda X, Y, d_in=d_in: one_level(X, Y, U, V, W, d_in, scale)  # noqa: E731
-            acc = acc + one_level(A, B, U, V, W, d_out, scale, mult=inner)
-    return acc / len(draws) ** 2
-
-
 # ----------------------------------------------------------------------------
 # Emulated low precision (Section 2.2 floating point model; Example 7)
 # ----------------------------------------------------------------------------

@@ -20,6 +20,44 @@ def gate(leaf: str, n0: int, L: int, N: int) -> float:
     return GATE_T[leaf] * g**L / np.sqrt(N)
 
 
+def entrywise_bound(A, B, n0: int, L: int, mixed: bool = False, rows=None, cols=None):
+    """Entrywise scale of the rounding error of C = F^(L)(A, B), in fp64.
+
+    Plain: (|A||B|)_ij, the scale of the standard product's error.  Mixed: the recursion adds
+    the n0^L x n0^L grid of m x m blocks of A (and of B) into the leaf operands, so an entry
+    of C also carries rounding error of every block row and column it is mixed with; the scale
+    is (Abar Bbar)_{i mod m, j mod m} with Abar = sum of |A| over the blocks (m x m).  The
+    mixed form is the one that holds for badly scaled rows and columns.  With rows/cols the
+    bound of those entries only."""
+    A = np.abs(np.asarray(A, dtype=np.float64))
+    B = np.abs(np.asarray(B, dtype=np.float64))
+    N = A.shape[0]
+    if not mixed:
+        if rows is None:
+            return A @ B
+        return np.einsum("sk,ks->s", A[rows], B[:, cols])
+    q = n0**L
+    m = N // q
+    Ab = A.reshape(q, m, q, m).sum(axis=(0, 2))
+    Bb = B.reshape(q, m, q, m).sum(axis=(0, 2))
+    if rows is None:
+        P = Ab @ Bb
+        return np.tile(P, (q, q))
+    rows, cols = np.asarray(rows) % m, np.asarray(cols) % m
+    return np.einsum("sk,ks->s", Ab[rows], Bb[:, cols])
+
+
+def entrywise(C, Cref, A, B, n0: int, L: int, mixed: bool = False) -> float:
+    """max_ij |C - C_ref|_ij / bound_ij (entrywise_bound); compared with the gate's t g^L."""
+    return float(np.max(np.abs(C - Cref) / entrywise_bound(A, B, n0, L, mixed)))
+
+
+def egate(leaf: str, n0: int, L: int) -> float:
+    """Entrywise gate t g^L (t and g of the normwise gate)."""
+    g = 2.0 if n0 == 2 else 3.0
+    return GATE_T[leaf] * g**L
+
+
 def normwise(C, Cref, A, B) -> float:
     return float(np.linalg.norm(C - Cref) / (np.linalg.norm(A) * np.linalg.norm(B)))
 

@@ -1,27 +1,58 @@
 """Parity at the measured sizes, in the configuration bench.py times: each product of the fp32
 sweep (Strassen n = 8192, L = 1..4; Laderman n = 6561, L = 1..3; perturbed Strassen n = 4096,
-L = 1..3; 3xbf16 leaves, per-node draws, automatic decode) and of the precision sweep
+L = 1..3; bf16x6 leaves, per-node draws, automatic decode) and of the precision sweep
 (Strassen n = 16384, every leaf mode), compared with the oracle's randomized recursion with the
 same draws on sampled entries (the oracle evaluates single entries of the full-size product).
 
-The gate is t g^L relative to ||AB|| (t per leaf mode, g = 2 per level for n0 = 2, 3 for n0 = 3).
-For the zero-mean N(0,1) inputs it is checked in its normwise form
-||C - C_oracle||_F / (||A||_F ||B||_F) <= t g^L / sqrt(N) (there ||AB||_F ~ ||A||_F ||B||_F / sqrt(N)),
-with ||C - C_oracle||_F estimated from the sampled entries as N times their root mean square.
-For the entrywise-positive scaled inputs ||AB||_F ~ ||A||_F ||B||_F and the relative form is
-checked directly on the sampled entries."""
+Samples: 1024 entries per product.  Beside uniformly drawn ones they hold every pairing of
+special rows and columns: the first and last, both sides of leaf-block boundaries
+(k m - 1, k m) and the tile edges of the leaf kernels inside a leaf (offsets 127, 128, 255,
+256), so that a wrong tile edge, padding column or leaf boundary is sampled.
+
+Gates (t per leaf mode, g = 2 per level for n0 = 2, 3 for n0 = 3):
+  * normwise ||C - C_oracle||_F / (||A||_F ||B||_F) <= t g^L / sqrt(N), with ||C - C_oracle||_F
+    estimated from the sampled entries as N times their root mean square;
+  * entrywise |C - C_oracle|_ij <= t g^L bound_ij on every sampled entry (bound as in
+    tests/_helpers.entrywise_bound: (|A||B|)_ij on zero-mean inputs, the block-mixed form on the
+    badly scaled ones).
+The two-piece 3xbf16 split keeps 16 significant bits of each leaf operand; on the entrywise
+positive scaled inputs its error (about 1e-5 relative to ||AB||, which there is about
+||A|| ||B||) does not cancel, and it is gated in the relative form ||C - C_oracle|| / ||AB|| <= t g^L
+only."""
 import numpy as np
 import pytest
 import torch
 
-from oracle import rbc_oracle as o
 from rbc_inputs import formula_by_name
 
-from ._helpers import gate
+from ._helpers import egate, entrywise_bound, gate
+from ._oracle_pool import oracle_entries
 
 pytestmark = pytest.mark.gpu
 
-SAMPLES = 32
+SAMPLES = 1024
+
+
+def sample_entries(n, m, seed):
+    """SAMPLES (row, col) pairs: every pairing of the special indices (first, last, both sides of
+    leaf boundaries, tile edges inside the first and last leaf block), then uniform ones."""
+    q = n // m
+    special = {0, n - 1}
+    for k in sorted({1, q // 2, q - 1}):
+        if 0 < k < q:
+            special |= {k * m - 1, k * m}
+    for base in (0, (q - 1) * m):
+        for t in (127, 128, 255, 256):
+            if t < m:
+                special.add(base + t)
+    sp = np.array(sorted(special))
+    rows, cols = np.meshgrid(sp, sp, indexing="ij")
+    rows, cols = rows.ravel()[:SAMPLES], cols.ravel()[:SAMPLES]
+    rng = np.random.default_rng(seed)
+    extra = SAMPLES - rows.size
+    rows = np.concatenate([rows, rng.integers(0, n, extra)])
+    cols = np.concatenate([cols, rng.integers(0, n, extra)])
+    return rows, cols
 
 
 @pytest.fixture(scope="module")
@@ -42,21 +73,25 @@ def _bench_inputs(n):
     return A, B
 
 
-def _sampled_normwise(rbc, name, n, L, seed, A, B, leaf, fseed=7):
+def _sampled_normwise(rbc, name, n, L, seed, A, B, leaf, fseed=7, mixed=False):
+    """(normwise estimate, n0, relative rms error, max entrywise ratio |dC| / bound) over the
+    sampled entries."""
     U, V, W = formula_by_name(name, seed=fseed)
+    n0 = U.shape[0]
     plan = rbc.Plan(U, V, W, levels=L, seed=seed)
     Ad, Bd = A.cuda(), B.cuda()
     C = rbc.matmul(plan, Ad, Bd, leaf=rbc.LEAF_NAMES[leaf])
-    rng = np.random.default_rng(n + 31 * L)
-    rows, cols = rng.integers(0, n, SAMPLES), rng.integers(0, n, SAMPLES)
+    rows, cols = sample_entries(n, n // n0**L, n + 31 * L)
     got = C[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")].double().cpu().numpy()
     del C, Ad, Bd
     torch.cuda.empty_cache()
     An, Bn = A.double().numpy(), B.double().numpy()
-    want = o.rbc_entries(An, Bn, o.Plan(U, V, W, levels=L, seed=seed), rows, cols)
+    want = oracle_entries(An, Bn, U, V, W, L, seed, rows, cols)
+    bound = entrywise_bound(An, Bn, n0, L, mixed, rows, cols)
     est = n * np.sqrt(np.mean((got - want) ** 2))
     rel = float(np.sqrt(np.mean((got - want) ** 2) / np.mean(want**2)))
-    return est / (np.linalg.norm(An) * np.linalg.norm(Bn)), U.shape[0], rel
+    ent = float(np.max(np.abs(got - want) / bound))
+    return est / (np.linalg.norm(An) * np.linalg.norm(Bn)), n0, rel, ent
 
 
 SWEEP = [("strassen", 8192, L) for L in (1, 2, 3, 4)] + [("laderman", 6561, L) for L in (1, 2, 3)] + \
@@ -66,31 +101,39 @@ SWEEP = [("strassen", 8192, L) for L in (1, 2, 3, 4)] + [("laderman", 6561, L) f
 @pytest.mark.parametrize("name,n,L", SWEEP)
 def test_sweep_sampled_parity(rbc, name, n, L):
     A, B = _bench_inputs(n)
-    err, n0, _ = _sampled_normwise(rbc, name, n, L, 2024 + L, A, B, "3xbf16")
-    assert err <= gate("3xbf16", n0, L, n), (name, n, L, err)
+    err, n0, _, ent = _sampled_normwise(rbc, name, n, L, 2024 + L, A, B, "bf16x6")
+    assert err <= gate("bf16x6", n0, L, n), (name, n, L, err)
+    assert ent <= egate("bf16x6", n0, L), (name, n, L, ent)
 
 
-@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "f32"])
+@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f32"])
 def test_precision_sweep_sampled_parity(rbc, leaf):
     n, L = 16384, 2
     g = torch.Generator(device="cpu")
     g.manual_seed(16384)
     A = torch.randn((n, n), generator=g, dtype=torch.float32)
     B = torch.randn((n, n), generator=g, dtype=torch.float32)
-    err, n0, _ = _sampled_normwise(rbc, "strassen", n, L, 2024 + L, A, B, leaf)
+    err, n0, _, ent = _sampled_normwise(rbc, "strassen", n, L, 2024 + L, A, B, leaf)
     assert err <= gate(leaf, n0, L, n), (leaf, err)
+    assert ent <= egate(leaf, n0, L), (leaf, ent)
 
 
-def test_hard_inputs_sampled_parity(rbc):
+@pytest.mark.parametrize("name,L,leaf", [("strassen", 2, "bf16x6"), ("laderman", 2, "bf16x6"),
+                                         ("strassen", 2, "3xbf16")])
+def test_hard_inputs_sampled_parity(rbc, name, L, leaf):
     """The badly scaled case: Uniform[0,1] with rows of A and columns of B scaled by
     10^U(-3,3)."""
     from rbc_inputs.matrices import matrix_pair
-    n, L = 8192, 2
+    n = 8192 if name == "strassen" else 6561
     Ah, Bh = matrix_pair("hard", n, 9)
     A = torch.tensor(Ah, dtype=torch.float32)
     B = torch.tensor(Bh, dtype=torch.float32)
-    _, n0, rel = _sampled_normwise(rbc, "strassen", n, L, 77, A, B, "3xbf16")
-    assert rel <= gate("3xbf16", n0, L, n) * np.sqrt(n), rel   # = t g^L relative to ||AB||
+    err, n0, rel, ent = _sampled_normwise(rbc, name, n, L, 77, A, B, leaf, mixed=True)
+    assert ent <= egate(leaf, n0, L), (leaf, ent)
+    if leaf == "3xbf16":
+        assert rel <= gate(leaf, n0, L, n) * np.sqrt(n), rel   # = t g^L relative to ||AB||
+    else:
+        assert err <= gate(leaf, n0, L, n), err
 
 
 @pytest.mark.parametrize("n,L,decode", [(46400, 1, 2), (46400, 1, 1), (47104, 2, 2)])

@@ -1,6 +1,7 @@
-"""Serving queue (rbc_queue_* / rbc_batch_submit / rbc_batch_poll): every request's result is
-the same alone and in the mix (concurrent admission, overlapping streams) within its leaf
-mode's tolerance; admission never exceeds the workspace cap; failures are reported per
+"""Serving queue (rbc_queue_* / rbc_batch_submit / rbc_batch_poll): every request's result in
+the mix (concurrent admission, overlapping streams, grouped leaf launches) matches the FP64
+oracle's recursion with the same draws within its leaf mode's gates, and is the same as the
+request computed alone; admission never exceeds the workspace cap; failures are reported per
 ticket without disturbing the other requests."""
 import time
 
@@ -8,7 +9,9 @@ import numpy as np
 import pytest
 import torch
 
-from ._helpers import formula, gate, normwise
+from oracle import rbc_oracle as o
+
+from ._helpers import egate, entrywise, formula, gate, normwise, oracle_plan
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +28,9 @@ def rbc():
 MIX = [("strassen", 1, 512, "bf16"), ("laderman", 1, 3 * 128, "3xbf16"), ("noisy-strassen", 2, 1024, "3xbf16"),
        ("strassen", 3, 8 * 96, "bf16"), ("laderman", 2, 9 * 64, "bf16"), ("strassen", 2, 4 * 200, "f32"),
        ("strassen", 1, 2048, "3xbf16"), ("noisy-strassen", 1, 2 * 300, "tf32"), ("laderman", 1, 3 * 200, "f16"),
-       ("strassen", 2, 1536, "bf16"), ("strassen", 1, 256, "f32"), ("laderman", 2, 9 * 128, "3xbf16")]
+       ("strassen", 2, 1536, "bf16"), ("strassen", 1, 256, "f32"), ("laderman", 2, 9 * 128, "3xbf16"),
+       ("strassen", 2, 4 * 256, "bf16x6"), ("laderman", 1, 3 * 256, "bf16x6"), ("strassen", 1, 512, "bf16"),
+       ("strassen", 1, 512, "bf16"), ("noisy-strassen", 2, 4 * 128, "bf16x6"), ("strassen", 1, 2 * 384, "bf16x6")]
 
 
 def _requests(rbc, seed):
@@ -65,10 +70,17 @@ def test_same_alone_and_in_the_mix(rbc):
     torch.cuda.synchronize()
     st = q.stats()
     assert st["completed"] == len(reqs) and st["peak_running"] >= 2
-    for (plan, A, B, leaf, name, n0, L, N), a, m in zip(reqs, alone, outs):
+    for i, ((plan, A, B, leaf, lname, n0, L, N), a, m) in enumerate(zip(reqs, alone, outs)):
         An, Bn = A.double().cpu().numpy(), B.double().cpu().numpy()
-        err = normwise(m.double().cpu().numpy(), a.double().cpu().numpy(), An, Bn)
-        assert err <= gate(name, n0, L, N), (name, L, N, err)
+        mix = m.double().cpu().numpy()
+        # against the oracle's recursion with the request's own draws
+        U, V, W = formula(MIX[i][0], seed=i)
+        ref = o.rbc(An, Bn, oracle_plan(U, V, W, L, 21 + i))
+        assert normwise(mix, ref, An, Bn) <= gate(lname, n0, L, N), (i, lname)
+        assert entrywise(mix, ref, An, Bn, n0, L) <= egate(lname, n0, L), (i, lname)
+        # and the same as alone
+        err = normwise(mix, a.double().cpu().numpy(), An, Bn)
+        assert err <= gate(lname, n0, L, N), (lname, L, N, err)
     q.close()
 
 
