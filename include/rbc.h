@@ -238,11 +238,21 @@ size_t rbc_realization_errors_work_size(int64_t K, int64_t N);
  * capture.  All calls share the one array and it keeps the previous call's contents (only
  * the status word is cleared per call), so calls whose device work overlaps -- on
  * different streams or threads -- race and give wrong results: order them on one stream.
- * The status word read by rbc_workspace_check lives at the start of the array. */
+ * The address is cached per device for the life of the process: resetting the device
+ * (cudaDeviceReset) after the first call is not supported.  The device status word of the
+ * bounded waits lives at the start of the array: read it with rbc_static_scratch_check. */
 rbc_status rbc_matmul_static(rbc_plan_t plan, const void* A, const void* B, void* C, int64_t N,
                              int64_t lda, int64_t ldb, int64_t ldc, int io_dtype, int leaf_dtype,
                              void* stream);
 size_t rbc_static_scratch_bytes(void);
+/* rbc_workspace_check on the static array of the current device: waits for `stream`, copies
+ * the status word of the calls that used the array to *device_status (0, or RBC_ETIMEOUT when
+ * a bounded wait inside a kernel expired and the result is invalid) and clears it.
+ * Synchronizes the stream. */
+rbc_status rbc_static_scratch_check(void* stream, int* device_status);
+/* Device address of the static array on the current device (NULL on error), e.g. to pass it
+ * as the workspace of rbc_matmul_ex for its options; the sharing rules above apply. */
+void* rbc_static_scratch_ptr(void);
 
 /* Grouped batch of independent products with fp32 I/O and tensor-core leaves (many
  * instances of uneven sizes, formulas, depths and seeds).  Each instance follows Section
@@ -297,12 +307,16 @@ rbc_status rbc_group_configure(rbc_group_t group, const rbc_group_tuning* cfg);
 void rbc_group_destroy(rbc_group_t group);
 
 /* Serving queue: independent products submitted as they arrive and served with continuous
- * admission.  A worker thread admits requests in arrival order as soon as a stream and enough
- * of the queue's device workspace pool are free (the pool is one region of `workspace_cap`
- * bytes, allocated at creation); admitted requests run on their own streams, so work from
- * requests that arrived while others were running overlaps on the device.  Each request is
- * computed exactly as rbc_matmul computes it.  Submit and poll may be called from any host
- * thread; poll never blocks. */
+ * batching.  A worker thread admits requests in arrival order as soon as enough of the queue's
+ * device workspace pool is free (the pool is one region of `workspace_cap` bytes, allocated at
+ * creation); a request that does not fit may be passed by later ones that do, at most 32 times,
+ * after which admission waits for it.  Small requests (N <= 2048) with the same tensor-core leaf
+ * mode admitted together form one unit whose leaf products share one grouped launch (the
+ * decode then runs level by level); every other request is a unit of its own, computed
+ * exactly as rbc_matmul computes it.  Units run on their own streams (one of `streams`), so
+ * work from requests that arrived while others were running overlaps on the device.  Submit
+ * and poll may be called from any host thread; the queue's lock is never held while work is
+ * enqueued, and poll never blocks. */
 typedef struct rbc_queue_s* rbc_queue_t;
 
 typedef struct {
@@ -315,10 +329,10 @@ typedef struct {
 } rbc_request;
 
 typedef struct {
-  int64_t pending, running;
+  int64_t pending, running;      /* requests waiting / in flight                                */
   uint64_t admitted, completed;
   size_t workspace_used, workspace_peak, workspace_cap;
-  int peak_running;
+  int peak_running;              /* most requests in flight at once                             */
 } rbc_queue_info;
 
 /* Create a queue on `device` with a workspace pool of workspace_cap bytes (one cudaMalloc)

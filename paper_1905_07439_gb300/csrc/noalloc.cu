@@ -11,7 +11,10 @@
 // The array is a file-scope __device__ object: every GPU that loads this library holds
 // kStaticScratchBytes of it until the process exits.  Host code must not use the symbol
 // itself as a pointer (on the host it is only a stand-in for the device object); the
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address is looked up once per device with cudaGetSymbolAddress and cached for the
+// life of the process (a device reset after the first call would leave it stale).  The
+// status word of the bounded device waits sits at the start of the array, like at the start
+// of a workspace; rbc_static_scratch_check reads and clears it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -66,6 +69,19 @@ rbc_status rbc_matmul_static(rbc_plan_t plan, const void* A, const void* B, void
   rbc_status s = scratch_address(&scratch);
   if (s != RBC_OK) return s;
   return rbc_matmul(plan, A, B, C, N, lda, ldb, ldc, io_dtype, leaf_dtype, scratch, kStaticScratchBytes, stream);
+}
+
+void* rbc_static_scratch_ptr(void) {
+  void* scratch = nullptr;
+  return scratch_address(&scratch) == RBC_OK ? scratch : nullptr;
+}
+
+rbc_status rbc_static_scratch_check(void* stream, int* device_status) {
+  if (!device_status) return rbc::fail(RBC_EINVAL, "null argument");
+  void* scratch = nullptr;
+  rbc_status s = scratch_address(&scratch);
+  if (s != RBC_OK) return s;
+  return rbc_workspace_check(scratch, stream, device_status);
 }
 
 }  // extern "C"

@@ -98,6 +98,8 @@ SIGNATURES = {
     "rbc_matmul_static": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int,
                                     C.c_int, _P]),
     "rbc_static_scratch_bytes": (C.c_size_t, []),
+    "rbc_static_scratch_check": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "rbc_static_scratch_ptr": (C.c_void_p, []),
     "rbc_norms": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P,
                             C.c_size_t, _P]),
     "rbc_norms_work_size": (C.c_size_t, []),
