@@ -180,7 +180,7 @@ class ClockSampler:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the step's ten leaf launches,
 # summed over one ncu capture of the full sweep, keyed by (leaf mode, library version): a
 # capture describes the kernel it measured only, so another library version reports null.
-LEAF_TRAFFIC_STEP = {}
+LEAF_TRAFFIC_STEP = {("bf16x6", 200): 46_604_675_328}
 # Stored panels per leaf operand and tensor-core products per leaf product of each leaf mode.
 LEAF_PANELS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 2, "3xtf32": 2, "bf16x6": 3}
 LEAF_PRODUCTS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 3, "3xtf32": 3, "bf16x6": 6}
