@@ -21,7 +21,8 @@
 // One-level passes of the built-in formulas (formulas.h) have the formula's sparsity compiled
 // in and apply the node's signed permutation to the operands (encode_fixed_kernel,
 // decode_fixed_kernel); one-level fp32 decodes of other n0 >= 3 formulas use nonzero lists
-// (decode_sparse_kernel).
+// (decode_sparse_kernel).  fp32 encodes of Laderman's formula cover two levels per pass, the
+// first level held in shared memory (encode_deep_kernel).
 //
 // Intermediates use the padded column layout of level_kernels.cuh with zero padding, so the
 // passes that read them take the branch-free vector variant (FAST) whatever m is.
@@ -891,6 +892,168 @@ __global__ void __launch_bounds__(kThreadsX) decode_fixed_kernel(const __grid_co
   }
 }
 
+// ------------------------------------------------------------------ built-in formulas, two levels
+// Two-level encode pass of a built-in formula with the intermediate level in shared memory.  A
+// CTA owns kDeepPos consecutive output positions of one output row y, for one parent:
+//   phase 1: thread (tau, g) -- tau = (k2, l2) one of the n0^2 sub-blocks of the second level,
+//            g a group of four positions -- loads the n0^2 first-level blocks (k1, l1) at
+//            sub-block tau (in the order of the parent's signed permutations, as the one-level
+//            pass does), forms every first-level child S_r1 = sum u_{k'l'r1} [...] and writes it
+//            to shared memory;
+//   phase 2: thread (r1, g) reads the n0^2 sub-blocks of child r1 at its positions (in the order
+//            of r1's own signed permutations) and forms the R grandchildren (r1, r2), the
+//            outputs, stored in the leaf type.
+// The first level's result never leaves the SM, so the pass moves the bytes of one level's
+// input and the second level's output only.  Terms are the formula's nonzeros in the
+// one-level passes' order.
+constexpr int kDeepPos = 128;  // output positions per CTA (32 groups of four)
+
+// Draw set of the node at relative depth j in {0, 1} below launch parent p with path q.
+template <typename Tc>
+__device__ __forceinline__ uint64_t subtree_draw(const Tables<Tc>& t, const PassArgs& a, int64_t p, int j, int q) {
+  int64_t real = 0, hp = a.node_first + p;
+  if (a.real_parents > 0) {
+    real = p / a.real_parents;
+    hp = a.node_first + (p - real * a.real_parents);
+  }
+  const uint64_t* draws = t.draw + real * a.real_draws;
+  if (t.per_level) return draws[a.depth + j];
+  const int64_t heap = j == 0 ? hp : hp * t.R + 1 + q;  // child q of hp: hp R + q + 1
+  return draws[a.dbase[j] + (heap - a.dfirst[j])];
+}
+
+template <typename Tin, class F, int TENSOR, int S>
+__global__ void __launch_bounds__(F::n0 * F::n0 * (kDeepPos / 4))
+    encode_deep_kernel(const __grid_constant__ Tables<float> t, const PassArgs a) {
+  constexpr int N0 = F::n0, R = F::R, NN = N0 * N0, VEC = 4, G = kDeepPos / VEC, THREADS = NN * G;
+  constexpr int CR = TENSOR == 1 ? 1 : 0, CC = TENSOR == 0 ? 1 : 2;  // row / column streams
+  using Tout = typename StoreType<S>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* inter = reinterpret_cast<float*>(smem_raw);  // [r1][tau][position]
+  const int tid = threadIdx.x;
+  const int64_t y = blockIdx.y, x0 = (int64_t)blockIdx.x * kDeepPos;
+  const int64_t outs = a.outs_per_parent;  // R^2
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    Tout* Yp = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
+    auto emitter = [&](int64_t x) {
+      EncodeEmitV<float, S, VEC> e;
+      e.Y = Yp;
+      e.strideY = a.strideY;
+      e.off = y * a.ldy + x;
+      e.kpanel = a.kpanel;
+      e.split = a.split;
+      e.vec = a.vstore != 0;
+      e.avail = a.cols_out - x;
+      return e;
+    };
+    if (y >= a.nb) {  // a padding row of every output: zeros
+      const float z[VEC] = {};
+      for (int item = tid; item < R * G; item += THREADS) {
+        const int r1 = item / G, g = item - r1 * G;
+        const int64_t x = x0 + g * VEC;
+        if (x >= a.cols_out) continue;
+        EncodeEmitV<float, S, VEC> emit = emitter(x);
+        for (int r2 = 0; r2 < R; ++r2) emit(r1 * R + r2, z);
+      }
+      continue;
+    }
+    // ---- phase 1: first level into shared memory
+    {
+      const int tau = tid / G, g = tid - tau * G;
+      const int k2 = tau / N0, l2 = tau - k2 * N0;
+      const int64_t x = x0 + g * VEC;
+      const int64_t xs = x % a.seg, avail_in = a.mval - xs;
+      float in[NN][VEC];
+      if (x < a.cols_out && avail_in > 0) {
+        const uint64_t w = subtree_draw(t, a, p, 0, 0);
+        int ir[N0], ic[N0];
+        float sr[N0], sc[N0];
+        inverse_stream<float, N0>(w, CR, ir, sr);
+        inverse_stream<float, N0>(w, CC, ic, sc);
+        const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
+        const int64_t xsrc = a.plain ? logical_col(x, a.seg, a.mval) : x;
+        const bool full = a.vload && avail_in >= VEC;
+#pragma unroll
+        for (int kp = 0; kp < N0; ++kp)
+#pragma unroll
+          for (int lp = 0; lp < N0; ++lp) {
+            const Tin* src = X + ((ir[kp] * N0 + k2) * a.nb + y) * a.ldx + (ic[lp] * N0 + l2) * colstep + xsrc;
+            Tin raw[VEC];
+            if (full) {
+              load_vec<Tin, VEC>(raw, src);
+            } else {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) raw[v] = (v < avail_in) ? src[v] : (Tin)0;
+            }
+            const float sg = sr[kp] * sc[lp];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) in[kp * N0 + lp][v] = sg * (float)raw[v];
+          }
+      } else {
+#pragma unroll
+        for (int e = 0; e < NN; ++e)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) in[e][v] = 0.f;
+      }
+      static_for<0, R>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        float acc[VEC] = {};
+        static_for<0, NN>([&](auto ee) {
+          constexpr int e = decltype(ee)::value;
+          constexpr int c = TENSOR == 0 ? F::U[e * R + r] : F::V[e * R + r];
+          if constexpr (c != 0) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = acc[v] + (float)c * in[e][v];
+          }
+        });
+        *reinterpret_cast<float4*>(inter + ((size_t)(r * NN + tau) * kDeepPos + g * VEC)) =
+            make_float4(acc[0], acc[1], acc[2], acc[3]);
+      });
+    }
+    __syncthreads();
+    // ---- phase 2: second level from shared memory to the outputs
+    for (int item = tid; item < R * G; item += THREADS) {
+      const int r1 = item / G, g = item - r1 * G;
+      const int64_t x = x0 + g * VEC;
+      if (x >= a.cols_out) continue;
+      const uint64_t w = subtree_draw(t, a, p, 1, r1);
+      int ir[N0], ic[N0];
+      float sr[N0], sc[N0];
+      inverse_stream<float, N0>(w, CR, ir, sr);
+      inverse_stream<float, N0>(w, CC, ic, sc);
+      float in[NN][VEC];
+#pragma unroll
+      for (int kp = 0; kp < N0; ++kp)
+#pragma unroll
+        for (int lp = 0; lp < N0; ++lp) {
+          const float4 v4 = *reinterpret_cast<const float4*>(
+              inter + ((size_t)(r1 * NN + ir[kp] * N0 + ic[lp]) * kDeepPos + g * VEC));
+          const float sg = sr[kp] * sc[lp];
+          in[kp * N0 + lp][0] = sg * v4.x;
+          in[kp * N0 + lp][1] = sg * v4.y;
+          in[kp * N0 + lp][2] = sg * v4.z;
+          in[kp * N0 + lp][3] = sg * v4.w;
+        }
+      EncodeEmitV<float, S, VEC> emit = emitter(x);
+      static_for<0, R>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        float acc[VEC] = {};
+        static_for<0, NN>([&](auto ee) {
+          constexpr int e = decltype(ee)::value;
+          constexpr int c = TENSOR == 0 ? F::U[e * R + r] : F::V[e * R + r];
+          if constexpr (c != 0) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = acc[v] + (float)c * in[e][v];
+          }
+        });
+        emit(r1 * R + r, acc);
+      });
+    }
+    __syncthreads();  // shared memory is reused by the next parent
+  }
+}
+
 inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
   const int64_t span = (int64_t)kThreadsX * vec;
@@ -930,6 +1093,25 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   // The passes write zeros into every padding column of the intermediates, so whole vectors
   // read from a padded-layout input are exact even where they run past the valid columns.
   const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0 && (a.plain ? a.mval % VEC == 0 : true);
+  if constexpr (G == 2 && N0 == 3 && std::is_same_v<Tc, float>) {
+    if (a.formula == LadermanFormula::id) {
+      using F = LadermanFormula;
+      constexpr int threads = F::n0 * F::n0 * (kDeepPos / 4);
+      const size_t smem_deep = (size_t)F::R * F::n0 * F::n0 * kDeepPos * sizeof(float);
+      const int64_t gz = a.parents < 65535 ? a.parents : 65535;
+      if (a.rows_out > 65535) return cudaErrorInvalidValue;
+      const dim3 grid((unsigned)((a.cols_out + kDeepPos - 1) / kDeepPos), (unsigned)a.rows_out, (unsigned)gz);
+      // four positions per thread: alignment for 16-byte loads and 4-element stores
+      const bool x4 = a.plain ? (a.nb % 4 == 0 && (a.mval % 4 == 0 || a.cols_out <= a.seg)) : a.xcol % 4 == 0;
+      a.vload = x4 && a.ldx % 4 == 0 && a.strideX % 4 == 0 && aligned(a.X, 4 * sizeof(Tin));
+      a.vstore = a.ldy % 4 == 0 && a.strideY % 4 == 0 && a.kpanel % 4 == 0 && aligned(a.Y, 4 * sizeof(Tout));
+      auto kern = a.tensor == 0 ? encode_deep_kernel<Tin, F, 0, S> : encode_deep_kernel<Tin, F, 1, S>;
+      cudaError_t e = prep(kern, smem_deep);
+      if (e != cudaSuccess) return e;
+      kern<<<grid, threads, smem_deep, st>>>(t, a);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (G == 1 && (N0 == 2 || N0 == 3)) {
     using F = std::conditional_t<N0 == 2, StrassenFormula, LadermanFormula>;
     if (a.formula == F::id) {
@@ -1066,6 +1248,9 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 // 220 registers, run at low occupancy, and measured slower than an extra pass over an
 // intermediate.
 int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
+int max_encode_levels_per_pass(int n0, int formula) {
+  return formula == kFormulaLaderman ? 2 : max_levels_per_pass(n0);
+}
 
 
 cudaError_t launch_encode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, int io, int store,

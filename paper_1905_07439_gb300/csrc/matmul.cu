@@ -46,10 +46,9 @@ int leaf_store(int leaf) {
 
 size_t store_bytes(int s) { return s == kStoreF64 ? 8 : (s == kStoreBF16 || s == kStoreF16) ? 2 : 4; }
 
-Passes plan_passes(int L, int n0) {
+Passes plan_passes(int L, int g) {
   Passes ps;
   if (L == 0) return ps;
-  const int g = max_levels_per_pass(n0);
   const int k = (L + g - 1) / g;
   int depth = 0;
   for (int i = 0; i < k; ++i) {
@@ -105,7 +104,8 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   }
   lo->K = lo->mp * (1 + lo->split);
   lo->seg = seg_pitch(lo->m);
-  lo->passes = plan_passes(L, n0);
+  lo->passes = plan_passes(L, io == RBC_IO_F32 ? max_encode_levels_per_pass(n0, p->builtin) : max_levels_per_pass(n0));
+  lo->dpasses = plan_passes(L, max_levels_per_pass(n0));
   const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;
   if (decode_req == 1 && !fused_ok) return fail(RBC_EUNSUPPORTED, "fused decode needs <= 1024 draw sets");
   if (decode_req == 0) {
@@ -138,8 +138,8 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   if (lo->decode == 2 && L > 0) {
     lo->M = off;
     off += align256((size_t)leaves * lo->mstride * lo->es_acc);
-    for (int i = 1; i < lo->passes.count; ++i) {
-      const int d = lo->passes.top[i];
+    for (int i = 1; i < lo->dpasses.count; ++i) {
+      const int d = lo->dpasses.top[i];
       const int64_t nd = lo->m * ipow(n0, L - d), wd = lo->seg * ipow(n0, L - d);
       lo->dec[d] = off;
       off += align256((size_t)(reals * ipow(R, d)) * nd * wd * lo->es_acc);
@@ -330,9 +330,9 @@ rbc_status decode_passes(const Reals& rs, const Layout& lo, void* C, int64_t ldc
                          cudaStream_t st) {
   const rbc_plan_s* p = rs.plan;
   const int L = p->L, R = p->R, n0 = p->n0;
-  for (int i = lo.passes.count - 1; i >= 0; --i) {
-    const int d = lo.passes.top[i], g = lo.passes.g[i];
-    const bool bottom = i + 1 == lo.passes.count;
+  for (int i = lo.dpasses.count - 1; i >= 0; --i) {
+    const int d = lo.dpasses.top[i], g = lo.dpasses.g[i];
+    const bool bottom = i + 1 == lo.dpasses.count;
     const int64_t n_par = lo.m * ipow(n0, L - d), nb = lo.m * ipow(n0, L - d - g);
     const int64_t w_par = lo.seg * ipow(n0, L - d), w_nb = lo.seg * ipow(n0, L - d - g);  // physical widths
     const int64_t P = ipow(R, d), outs = ipow(R, g);

@@ -35,7 +35,8 @@ struct Layout {
   int store = 0, decode = 0;  // decode: 1 fused, 2 staged passes
   int split = 0;              // extra panels of the leaf operands: 0 plain, 1 [hi | lo], 2 [b0 | b1 | b2]
   size_t es_io = 0, es_acc = 0, es_leaf = 0;
-  Passes passes;
+  Passes passes;   // encode passes, root first
+  Passes dpasses;  // decode passes (the same levels may be grouped differently)
   size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
   size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
   int64_t mstride = 0;  // elements from one leaf product to the next in M (mp^2)
@@ -55,7 +56,7 @@ struct Reals {
 
 bool is_tc_leaf(int leaf);
 int leaf_panels(int leaf);  // stored panels per leaf operand: 1, 2 (split modes) or 3 (bf16x6)
-Passes plan_passes(int L, int n0);
+Passes plan_passes(int L, int g);  // passes of at most g levels
 // reals > 1: the layout of that many realizations (staged decode only).
 rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo,
                        int64_t reals = 1);
