@@ -1248,8 +1248,11 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 // 220 registers, run at low occupancy, and measured slower than an extra pass over an
 // intermediate.
 int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
-int max_encode_levels_per_pass(int n0, int formula) {
-  return formula == kFormulaLaderman ? 2 : max_levels_per_pass(n0);
+int max_encode_levels_per_pass(int n0, int formula, int64_t m) {
+  // Laderman's formula: two levels (the first in shared memory), when the leaf rows fill the
+  // 128-position tiles reasonably (m >= 32)
+  if (formula == kFormulaLaderman && m >= 32) return 2;
+  return max_levels_per_pass(n0);
 }
 
 

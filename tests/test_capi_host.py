@@ -133,6 +133,22 @@ def test_workspace_sizes(rbc):
     assert ws4_3x - ws4 == panel and ws4_6x - ws4 == 2 * panel
 
 
+def test_laderman_encode_passes_cover_two_levels(rbc):
+    """fp32 encodes of Laderman's formula run two levels per pass once leaves reach 32 (the first
+    level in shared memory): at L = 3 only the depth-1 intermediate (23 blocks of 2187 rows in the
+    padded layout: 9 column segments of 243 padded to 244) is stored per operand; below m = 32
+    every level is a pass."""
+    U, V, W = laderman()
+    p3 = rbc.Plan(U, V, W, levels=3)
+    ws = p3.workspace_size(6561, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
+    leaves = 2 * 2 * 12167 * 256**2
+    body = 2 * 4 * 23 * 2187 * (9 * 244) + leaves
+    assert body <= ws <= body + 4096
+    small = rbc.Plan(U, V, W, levels=2)   # m = 27: one-level passes, depth-1 intermediate
+    ws2 = small.workspace_size(9 * 27, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
+    assert ws2 >= 2 * 4 * 23 * 81 * 84
+
+
 def test_empty_and_ragged_sizes_are_refused(rbc):
     """N must be a positive multiple of n0^L (the recursion splits N into n0^L equal blocks);
     an empty product and a ragged N are refused with RBC_EINVAL before any device memory is
