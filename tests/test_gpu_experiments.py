@@ -40,7 +40,9 @@ def _inputs(N, seed, dtype):
 # (formula, levels, N, scope, rand mode)
 CASES = [("noisy-strassen", 3, 80, "level", "full"), ("strassen", 2, 4 * 37, "node", "full"),
          ("laderman", 2, 9 * 11, "node", "sign"), ("noisy-strassen", 5, 320, "node", "perm"),
-         ("laderman", 1, 3 * 40, "level", "full"), ("strassen", 4, 16 * 9, "level", "none")]
+         ("laderman", 1, 3 * 40, "level", "full"), ("strassen", 4, 16 * 9, "level", "none"),
+         # leaves of 33 and 40: fp32 encodes of Laderman's formula run two-level passes
+         ("laderman", 2, 9 * 40, "level", "full"), ("laderman", 3, 27 * 33, "node", "full")]
 MODES = {"full": 0, "sign": 1, "perm": 2, "none": 3}
 
 
@@ -78,7 +80,7 @@ def test_batch_equals_single_calls(rbc, case, io):
 @pytest.mark.parametrize("leaf", ["bf16", "3xbf16", "tf32"])
 def test_batch_equals_single_calls_tensor_core_leaves(rbc, leaf):
     U, V, W = formula("laderman")
-    N, L, K = 9 * 24, 2, 5
+    N, L, K = 9 * 40, 2, 5   # leaves of 40: two-level encode passes
     plan = rbc.Plan(U, V, W, levels=L, seed=0)
     _, _, A, B = _inputs(N, 3, torch.float32)
     lf = rbc.LEAF_NAMES[leaf]

@@ -260,6 +260,25 @@ def test_error_within_emulated_precision(rbc, name, L, N, leaf):
     assert got <= 4.0 * emu + 1e-7, (got, emu)
 
 
+@pytest.mark.parametrize("L,m,scope", [(2, 31, o.DRAW_PER_NODE), (2, 32, o.DRAW_PER_NODE), (2, 33, o.DRAW_PER_LEVEL),
+                                       (2, 130, o.DRAW_PER_NODE), (3, 33, o.DRAW_PER_NODE), (3, 36, o.DRAW_PER_LEVEL)])
+@pytest.mark.parametrize("leaf", ["f32", "bf16x6", "bf16"])
+def test_laderman_two_level_encode(rbc, L, m, scope, leaf):
+    """fp32 encodes of Laderman's formula run two levels per pass for leaves of at least 32 (the
+    first level in shared memory, 128-position tiles): leaves across that threshold, ragged and
+    spanning two tiles, per-node and per-level draws, against the oracle."""
+    U, V, W = formula("laderman")
+    N = 3**L * m
+    A, B = matrix_pair("normal", N, seed=70 + m)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    plan = rbc.Plan(U, V, W, levels=L, seed=2 * m + L, draw_scope=scope)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, 2 * m + L, scope=scope))
+    C = gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_NAMES[leaf], 2)
+    assert normwise(C, ref, A, B) <= gate(leaf, 3, L, N)
+    assert entrywise(C, ref, A, B, 3, L) <= egate(leaf, 3, L)
+
+
 def test_workspace_status_word_clear_after_calls(rbc):
     import ctypes
     U, V, W = formula("strassen")
