@@ -22,7 +22,8 @@
 // in and apply the node's signed permutation to the operands (encode_fixed_kernel,
 // decode_fixed_kernel); one-level fp32 decodes of other n0 >= 3 formulas use nonzero lists
 // (decode_sparse_kernel).  fp32 encodes of Laderman's formula cover two levels per pass, the
-// first level held in shared memory (encode_deep_kernel).
+// first level held in shared memory (encode_deep_kernel); fp32 two-level decodes of Strassen's
+// formula hand the lower level to the upper one through shared memory (decode_deep_kernel).
 //
 // Intermediates use the padded column layout of level_kernels.cuh with zero padding, so the
 // passes that read them take the branch-free vector variant (FAST) whatever m is.
@@ -1054,6 +1055,114 @@ __global__ void __launch_bounds__(F::n0 * F::n0 * (kDeepPos / 4))
   }
 }
 
+// Two-level decode pass of Strassen's formula with the lower level handed over in shared memory.
+// A CTA owns kDeepPos consecutive positions of one child row y, for one parent:
+//   phase 1: item (r1, g) loads the R grandchildren (r1, r2) at its four positions (all R loads
+//            in flight at once), forms child r1's n0^2 blocks D_{i'j'} = sum_r2 w_{i'j'r2} M_(r1, r2)
+//            (r2 in order) and writes each, scaled and signed by r1's draws, to its sub-block
+//            (pi1^-1(i'), pi3^-1(j')) in shared memory;
+//   phase 2: item (tau, g) -- tau one of the n0^2 sub-blocks -- forms the parent's blocks
+//            sum_r1 w_{i'j'r1} child_r1[tau] (r1 in order) and stores them.
+// Small per-thread state (one child's R loads, n0^2 sums) keeps many CTAs, and so many loads, in
+// flight per SM.  The sums run over the formula's nonzeros in the one-level passes' order.
+template <class F>
+__global__ void __launch_bounds__(kThreadsX) decode_deep_kernel(const __grid_constant__ Tables<float> t,
+                                                                const PassArgs a) {
+  constexpr int N0 = F::n0, R = F::R, NN = N0 * N0, VEC = 4, G = kDeepPos / VEC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* inter = reinterpret_cast<float*>(smem_raw);  // [r1][tau][position]
+  const int tid = threadIdx.x;
+  const int64_t y = blockIdx.y, x0 = (int64_t)blockIdx.x * kDeepPos;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    // ---- phase 1: the lower level of each child r1 into shared memory
+    for (int item = tid; item < R * G; item += kThreadsX) {
+      const int r1 = item / G, g = item - r1 * G;
+      const int64_t x = x0 + g * VEC;
+      const int64_t xs = x % a.seg, avail = a.mval - xs;
+      if (x >= a.xcol || avail <= 0) continue;
+      DecodeFetch<float, float, VEC> fetch;
+      fetch.M = static_cast<const float*>(a.X) + (p * a.outs_per_parent + (int64_t)r1 * R) * a.strideX;
+      fetch.strideM = a.strideX;
+      fetch.off = y * a.ldx + x;
+      fetch.avail = avail;
+      fetch.vec = a.vload != 0;
+      float m[R][VEC];
+      static_for<0, R>([&](auto rr) { fetch(decltype(rr)::value, m[decltype(rr)::value]); });
+      float D[NN][VEC] = {};
+      static_for<0, R>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        static_for<0, NN>([&](auto ee) {
+          constexpr int e = decltype(ee)::value;
+          constexpr int c = F::W[e * R + r];
+          if constexpr (c != 0) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) D[e][v] = D[e][v] + (float)c * m[r][v];
+          }
+        });
+      });
+      const uint64_t w = subtree_draw(t, a, p, 1, r1);
+      int ir[N0], ic[N0];
+      float sr[N0], sc[N0];
+      inverse_stream<float, N0>(w, 0, ir, sr);
+      inverse_stream<float, N0>(w, 2, ic, sc);
+#pragma unroll
+      for (int ip = 0; ip < N0; ++ip)
+#pragma unroll
+        for (int jp = 0; jp < N0; ++jp) {
+          const float f = t.scale * sr[ip] * sc[jp];
+          const int e = ip * N0 + jp;
+          *reinterpret_cast<float4*>(inter + ((size_t)(r1 * NN + ir[ip] * N0 + ic[jp]) * kDeepPos + g * VEC)) =
+              make_float4(f * D[e][0], f * D[e][1], f * D[e][2], f * D[e][3]);
+        }
+    }
+    __syncthreads();
+    // ---- phase 2: the parent's level from shared memory
+    for (int item = tid; item < NN * G; item += kThreadsX) {
+      const int tau = item / G, g = item - tau * G;
+      const int i2 = tau / N0, j2 = tau - i2 * N0;
+      const int64_t x = x0 + g * VEC;
+      const int64_t xs = x % a.seg, avail = a.mval - xs;
+      if (x >= a.xcol || avail <= 0) continue;
+      float D[NN][VEC] = {};
+      static_for<0, R>([&](auto rr) {
+        constexpr int r = decltype(rr)::value;
+        const float4 v4 = *reinterpret_cast<const float4*>(inter + ((size_t)(r * NN + tau) * kDeepPos + g * VEC));
+        const float mv[VEC] = {v4.x, v4.y, v4.z, v4.w};
+        static_for<0, NN>([&](auto ee) {
+          constexpr int e = decltype(ee)::value;
+          constexpr int c = F::W[e * R + r];
+          if constexpr (c != 0) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) D[e][v] = D[e][v] + (float)c * mv[v];
+          }
+        });
+      });
+      const uint64_t w = subtree_draw(t, a, p, 0, 0);
+      int ir[N0], ic[N0];
+      float sr[N0], sc[N0];
+      inverse_stream<float, N0>(w, 0, ir, sr);
+      inverse_stream<float, N0>(w, 2, ic, sc);
+      float* P = static_cast<float*>(a.Y) + p * a.strideY;
+      const int64_t xdst = a.plain ? logical_col(x, a.seg, a.mval) : x;
+      const int64_t avail_st = a.plain ? avail : VEC;
+      const bool vs = a.vstore != 0;
+#pragma unroll
+      for (int ip = 0; ip < N0; ++ip)
+#pragma unroll
+        for (int jp = 0; jp < N0; ++jp) {
+          const float f = t.scale * sr[ip] * sc[jp];
+          float o[VEC];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) o[v] = f * D[ip * N0 + jp][v];
+          store_some<float, VEC>(P + ((ir[ip] * N0 + i2) * a.nb + y) * a.ldy + (ic[jp] * N0 + j2) * colstep + xdst,
+                                 o, vs, avail_st);
+        }
+    }
+    __syncthreads();  // shared memory is reused by the next parent
+  }
+}
+
 inline dim3 pass_grid(int64_t rows, int64_t cols, int64_t parents, int vec) {
   const int64_t gz = parents < 65535 ? parents : 65535;
   const int64_t span = (int64_t)kThreadsX * vec;
@@ -1170,6 +1279,22 @@ cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   // columns, so whole-vector loads are exact; a padded-layout parent takes whole-vector
   // stores, a plain one (C) only complete vectors.
   const bool fast = a.vload && a.vstore && (a.plain ? a.mval % VEC == 0 : true);
+  if constexpr (G == 2 && N0 == 2 && std::is_same_v<Tc, float> && std::is_same_v<Tm, float> &&
+                std::is_same_v<To, float>) {
+    if (a.formula == StrassenFormula::id) {
+      using F = StrassenFormula;
+      const size_t smem_deep = (size_t)F::R * F::n0 * F::n0 * kDeepPos * sizeof(float);
+      const int64_t gz = a.parents < 65535 ? a.parents : 65535;
+      if (a.nb > 65535) return cudaErrorInvalidValue;
+      const dim3 grid((unsigned)((a.xcol + kDeepPos - 1) / kDeepPos), (unsigned)a.nb, (unsigned)gz);
+      // four positions per thread: alignment for 16-byte loads and stores
+      const bool y4 = a.plain ? (a.nb % 4 == 0 && (a.mval % 4 == 0 || a.xcol <= a.seg)) : true;
+      a.vload = a.ldx % 4 == 0 && a.strideX % 4 == 0 && aligned(a.X, 16);
+      a.vstore = y4 && a.ldy % 4 == 0 && a.strideY % 4 == 0 && aligned(a.Y, 16);
+      decode_deep_kernel<F><<<grid, kThreadsX, smem_deep, st>>>(t, a);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (G == 1 && (N0 == 2 || N0 == 3) && std::is_same_v<Tm, Tc> && std::is_same_v<To, Tc>) {
     using F = std::conditional_t<N0 == 2, StrassenFormula, LadermanFormula>;
     if (a.formula == F::id) {

@@ -291,7 +291,7 @@ def test_workspace_status_word_clear_after_calls(rbc):
     assert st.value == 0
 
 
-@pytest.mark.parametrize("leaf,decode", [("bf16", 2), ("3xbf16", 2), ("bf16", 1)])
+@pytest.mark.parametrize("leaf,decode", [("bf16", 2), ("3xbf16", 2), ("bf16", 1), ("bf16x6", 2), ("bf16x6", 1)])
 def test_expired_wait_reports_timeout_and_the_context_survives(rbc, leaf, decode):
     """Failure detection without a fault.  With the stall test hook the leaf kernel issues no
     operand copies, so its MMA warp's bounded wait (2 s) expires: the kernel records
