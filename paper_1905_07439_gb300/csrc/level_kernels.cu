@@ -1055,8 +1055,8 @@ __global__ void __launch_bounds__(F::n0 * F::n0 * (kDeepPos / 4))
   }
 }
 
-// Two-level decode pass of Strassen's formula with the lower level handed over in shared memory.
-// A CTA owns kDeepPos consecutive positions of one child row y, for one parent:
+// Two-level decode pass of a built-in formula with the lower level handed over in shared memory.
+// A CTA owns POS consecutive positions of one child row y, for one parent:
 //   phase 1: item (r1, g) loads the R grandchildren (r1, r2) at its four positions (all R loads
 //            in flight at once), forms child r1's n0^2 blocks D_{i'j'} = sum_r2 w_{i'j'r2} M_(r1, r2)
 //            (r2 in order) and writes each, scaled and signed by r1's draws, to its sub-block
@@ -1065,14 +1065,14 @@ __global__ void __launch_bounds__(F::n0 * F::n0 * (kDeepPos / 4))
 //            sum_r1 w_{i'j'r1} child_r1[tau] (r1 in order) and stores them.
 // Small per-thread state (one child's R loads, n0^2 sums) keeps many CTAs, and so many loads, in
 // flight per SM.  The sums run over the formula's nonzeros in the one-level passes' order.
-template <class F>
+template <class F, int POS>
 __global__ void __launch_bounds__(kThreadsX) decode_deep_kernel(const __grid_constant__ Tables<float> t,
                                                                 const PassArgs a) {
-  constexpr int N0 = F::n0, R = F::R, NN = N0 * N0, VEC = 4, G = kDeepPos / VEC;
+  constexpr int N0 = F::n0, R = F::R, NN = N0 * N0, VEC = 4, G = POS / VEC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* inter = reinterpret_cast<float*>(smem_raw);  // [r1][tau][position]
   const int tid = threadIdx.x;
-  const int64_t y = blockIdx.y, x0 = (int64_t)blockIdx.x * kDeepPos;
+  const int64_t y = blockIdx.y, x0 = (int64_t)blockIdx.x * POS;
   const int64_t colstep = a.plain ? a.nb : a.xcol;
   for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
     // ---- phase 1: the lower level of each child r1 into shared memory
@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_deep_kernel(const __grid_con
         for (int jp = 0; jp < N0; ++jp) {
           const float f = t.scale * sr[ip] * sc[jp];
           const int e = ip * N0 + jp;
-          *reinterpret_cast<float4*>(inter + ((size_t)(r1 * NN + ir[ip] * N0 + ic[jp]) * kDeepPos + g * VEC)) =
+          *reinterpret_cast<float4*>(inter + ((size_t)(r1 * NN + ir[ip] * N0 + ic[jp]) * POS + g * VEC)) =
               make_float4(f * D[e][0], f * D[e][1], f * D[e][2], f * D[e][3]);
         }
     }
@@ -1127,7 +1127,7 @@ __global__ void __launch_bounds__(kThreadsX) decode_deep_kernel(const __grid_con
       float D[NN][VEC] = {};
       static_for<0, R>([&](auto rr) {
         constexpr int r = decltype(rr)::value;
-        const float4 v4 = *reinterpret_cast<const float4*>(inter + ((size_t)(r * NN + tau) * kDeepPos + g * VEC));
+        const float4 v4 = *reinterpret_cast<const float4*>(inter + ((size_t)(r * NN + tau) * POS + g * VEC));
         const float mv[VEC] = {v4.x, v4.y, v4.z, v4.w};
         static_for<0, NN>([&](auto ee) {
           constexpr int e = decltype(ee)::value;
@@ -1279,19 +1279,23 @@ cudaError_t dec_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   // columns, so whole-vector loads are exact; a padded-layout parent takes whole-vector
   // stores, a plain one (C) only complete vectors.
   const bool fast = a.vload && a.vstore && (a.plain ? a.mval % VEC == 0 : true);
-  if constexpr (G == 2 && N0 == 2 && std::is_same_v<Tc, float> && std::is_same_v<Tm, float> &&
+  if constexpr (G == 2 && (N0 == 2 || N0 == 3) && std::is_same_v<Tc, float> && std::is_same_v<Tm, float> &&
                 std::is_same_v<To, float>) {
-    if (a.formula == StrassenFormula::id) {
-      using F = StrassenFormula;
-      const size_t smem_deep = (size_t)F::R * F::n0 * F::n0 * kDeepPos * sizeof(float);
+    using F = std::conditional_t<N0 == 2, StrassenFormula, LadermanFormula>;
+    if (a.formula == F::id) {
+      constexpr int POS = N0 == 2 ? 128 : 64;  // positions per CTA (shared memory R n0^2 POS floats)
+      const size_t smem_deep = (size_t)F::R * F::n0 * F::n0 * POS * sizeof(float);
       const int64_t gz = a.parents < 65535 ? a.parents : 65535;
       if (a.nb > 65535) return cudaErrorInvalidValue;
-      const dim3 grid((unsigned)((a.xcol + kDeepPos - 1) / kDeepPos), (unsigned)a.nb, (unsigned)gz);
+      const dim3 grid((unsigned)((a.xcol + POS - 1) / POS), (unsigned)a.nb, (unsigned)gz);
       // four positions per thread: alignment for 16-byte loads and stores
       const bool y4 = a.plain ? (a.nb % 4 == 0 && (a.mval % 4 == 0 || a.xcol <= a.seg)) : true;
       a.vload = a.ldx % 4 == 0 && a.strideX % 4 == 0 && aligned(a.X, 16);
       a.vstore = y4 && a.ldy % 4 == 0 && a.strideY % 4 == 0 && aligned(a.Y, 16);
-      decode_deep_kernel<F><<<grid, kThreadsX, smem_deep, st>>>(t, a);
+      auto kern = decode_deep_kernel<F, POS>;
+      cudaError_t e = prep(kern, smem_deep);
+      if (e != cudaSuccess) return e;
+      kern<<<grid, kThreadsX, smem_deep, st>>>(t, a);
       return cudaGetLastError();
     }
   }
@@ -1373,6 +1377,13 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 // 220 registers, run at low occupancy, and measured slower than an extra pass over an
 // intermediate.
 int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
+int max_decode_levels_per_pass(int n0, int formula, int64_t m) {
+  // Laderman's formula: two levels (the lower handed over in shared memory), when the child rows
+  // fill the 64-position tiles reasonably (m >= 32)
+  if (formula == kFormulaLaderman && m >= 32) return 2;
+  return max_levels_per_pass(n0);
+}
+
 int max_encode_levels_per_pass(int n0, int formula, int64_t m) {
   // Laderman's formula: two levels (the first in shared memory), when the leaf rows fill the
   // 128-position tiles reasonably (m >= 32)

@@ -63,6 +63,9 @@ int max_levels_per_pass(int n0);
 // Levels an fp32 encode pass covers for leaf size m: two for Laderman's formula when m >= 32
 // (the first level held in shared memory, 128-position tiles), else max_levels_per_pass.
 int max_encode_levels_per_pass(int n0, int formula, int64_t m);
+// Levels an fp32 decode pass covers for leaf size m: two for Laderman's formula when m >= 32 (the
+// lower level handed over in shared memory, 64-position tiles), else max_levels_per_pass.
+int max_decode_levels_per_pass(int n0, int formula, int64_t m);
 // g = 0 is the identity pass of L = 0 (conversion and padding of the single leaf).
 cudaError_t launch_encode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, int io, int store,
                                cudaStream_t st);
