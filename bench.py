@@ -419,8 +419,10 @@ def run_ours(args):
         barrier()
         e_ms = a0.elapsed_time(a1) / args.steps
         step_ms = [round((a0 if k == 0 else marks[k - 1]).elapsed_time(marks[k]), 3) for k in range(args.steps)]
+        med = statistics.median(step_ms)
         e2e = {"value": round(world * eff_flops / (e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
                "ms_per_step": round(e_ms, 3), "step_ms": step_ms,
+               "median_step_value": round(world * eff_flops / (med * 1e-3) / 1e12, 3),
                "h2d_bytes_per_step": sum(2 * 4 * n * n for n in sorted({c[1] for c in cases})),
                "d2h_bytes_per_step": sum(4 * n * n for _, n, _ in cases)}
 
