@@ -1,7 +1,8 @@
 // Encode and decode passes of the recursion (Section 2.1.1, Eq. recursive-random-formula).
 // Each pass covers G consecutive levels (G <= 2 for n0 = 2, G = 1 for n0 >= 3, see
 // max_levels_per_pass), so that the intermediate operands of those levels never leave
-// registers.
+// registers.  fp32 encodes go deeper: up to four levels for n0 = 2 (encode_top_kernel) and two
+// for Laderman's formula (encode_deep_kernel).
 //
 // Table-driven passes (any formula): at the start of every parent, the CTA expands the
 // randomized tables of the parent's G-level subtree into shared memory (Prop. 10:
@@ -105,12 +106,12 @@ __host__ __device__ constexpr int coef_stride(int n0) { return (n0 * n0 + 3) / 4
 // Local id of the node at relative depth j with path prefix q: sum_{i<j} R^i + q.
 __device__ __forceinline__ int local_id(int R, int j, int q) { return subtree_nodes(R, j) + q; }
 
-// Expand the tables of the G-level subtree under launch parent p (at depth a.depth) into
-// coef[(local * R + r) * coef_stride(n0) + a * n0 + b] for tensor `which` (0 u^, 1 v^, 2 w^);
-// the row padding holds zeros.
-template <typename Tc>
-__device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, int which, int64_t p,
-                               Tc* coef) {
+// Expand coefficient rows of the subtree under launch parent p (at depth a.depth) into
+// coef[(row * R + r) * coef_stride(n0) + a * n0 + b] for tensor `which` (0 u^, 1 v^, 2 w^),
+// row = 0 .. rows-1 holding the node with local id local_of(row); the row padding holds zeros.
+template <typename Tc, class Map>
+__device__ void expand_rows(const Tables<Tc>& t, const PassArgs& a, int rows, int which, int64_t p, Tc* coef,
+                            Map local_of) {
   int64_t real = 0, hp = a.node_first + p;
   if (a.real_parents > 0) {
     real = p / a.real_parents;
@@ -118,15 +119,16 @@ __device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, in
   }
   const uint64_t* draws = t.draw + real * a.real_draws;
   const int R = t.R, n0 = t.n0, nn = n0 * n0, ns = coef_stride(n0);
-  const int total = subtree_nodes(R, G) * R * ns;
+  const int total = rows * R * ns;
   const Tc* base = which == 0 ? t.U : (which == 1 ? t.V : t.W);
   const int cr = which == 1 ? 1 : 0;  // row stream: pi1/s1 (u^, w^) or pi2/s2 (v^)
   const int cc = which == 0 ? 1 : 2;  // column stream: pi2/s2 (u^) or pi3/s3 (v^, w^)
   const Tc sc = which == 2 ? t.scale : (Tc)1;
   const int nthreads = blockDim.x * blockDim.y;
   for (int e = threadIdx.y * blockDim.x + threadIdx.x; e < total; e += nthreads) {
-    const int local = e / (R * ns);
-    const int rem = e - local * R * ns;
+    const int row = e / (R * ns);
+    const int rem = e - row * R * ns;
+    const int local = local_of(row);
     const int r = rem / ns, ab = rem - r * ns, ra = ab / n0, cb = ab - ra * n0;
     if (ab >= nn) {
       coef[e] = (Tc)0;
@@ -145,6 +147,15 @@ __device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, in
     const Tc v = base[(draw_perm(w, cr, ra) * n0 + draw_perm(w, cc, cb)) * R + r];
     coef[e] = sc * v * (Tc)draw_sign(w, cr, ra) * (Tc)draw_sign(w, cc, cb);
   }
+}
+
+// All rows of the G-level subtree under launch parent p, row = local id.
+struct IdentityRows {
+  __device__ __forceinline__ int operator()(int row) const { return row; }
+};
+template <typename Tc>
+__device__ void expand_subtree(const Tables<Tc>& t, const PassArgs& a, int G, int which, int64_t p, Tc* coef) {
+  expand_rows(t, a, subtree_nodes(t.R, G), which, p, coef, IdentityRows{});
 }
 
 // One child's coefficient row from shared memory, as 16-byte vectors.
@@ -381,6 +392,107 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
         for (int v = 0; v < VEC; ++v) in[k * W + l][v] = (Tc)raw[v];
       }
     EncodeWalk<Tc, N0, G, VEC>::go(coef, t.R, 0, 0, 0, in, emit);
+  }
+}
+
+// Encode passes of TOP + 2 levels for n0 = 2 (fp32 arithmetic, R <= kTop3MaxR).  The first TOP
+// levels (1 or 2) are split over the CTAs: CTA (tile, t) forms the node with path t at depth
+// TOP at its positions straight from the parent's 2^(TOP+2) x 2^(TOP+2) blocks (the u^
+// coefficients on the path are the same for the whole CTA, so zero terms load nothing), then
+// walks the two levels below that node in registers like the two-level pass.  The R^TOP CTAs of
+// one position tile are neighbours in the grid, so the parent's rows come from DRAM once and
+// are re-read from L2: no intermediate of those levels is written or read.
+// Shared tables (compact rows): 0 the node t, 1..R its children, R+1 the root, R+2 (TOP = 2)
+// the first-level node on t's path.
+template <int TOP>
+struct TopRows {
+  int R, t;
+  __device__ __forceinline__ int operator()(int row) const {
+    if (row == 0) return subtree_nodes(R, TOP) + t;
+    if (row <= R) return subtree_nodes(R, TOP + 1) + t * R + (row - 1);
+    if (row == R + 1) return 0;
+    return 1 + t / R;  // TOP == 2: first-level node r1 of t = r1 * R + r2
+  }
+};
+__host__ __device__ constexpr int top_rows(int R, int TOP) { return R + 1 + TOP; }
+
+template <typename Tin, typename Tc, int S, int TOP, int VEC, bool FAST>
+__global__ void __launch_bounds__(kThreadsX) encode_top_kernel(const __grid_constant__ Tables<Tc> t,
+                                                               const PassArgs a) {
+  constexpr int N0 = 2, WC = 4, NS = coef_stride(N0);
+  using Tout = typename StoreType<S>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc* coef = reinterpret_cast<Tc*>(smem_raw);
+  const int R = t.R;
+  const int RT = TOP == 1 ? R : R * R;
+  const int tp = (int)(blockIdx.x % (unsigned)RT);  // path of the first TOP levels
+  const int64_t tile = blockIdx.x / (unsigned)RT;
+  const int64_t colsv = (a.cols_out + VEC - 1) / VEC * VEC;
+  const int64_t pos = (tile * kThreadsX + threadIdx.x) * VEC;
+  const int64_t y = pos / colsv, x = pos - y * colsv;
+  const bool inside = y < a.rows_out && x < a.cols_out;
+  const int64_t outs = a.outs_per_parent;
+  const int64_t xs = x % a.seg;
+  const int64_t avail_in = a.mval - xs;
+  const int64_t xsrc = a.plain ? logical_col(x, a.seg, a.mval) : x;
+  const int64_t colstep = a.plain ? a.nb : a.xcol;
+  for (int64_t p = blockIdx.z; p < a.parents; p += gridDim.z) {
+    __syncthreads();
+    expand_rows(t, a, top_rows(R, TOP), a.tensor, p, coef, TopRows<TOP>{R, tp});
+    __syncthreads();
+    if (!inside) continue;
+    EncodeEmitV<Tc, S, VEC> emit;
+    emit.Y = static_cast<Tout*>(a.Y) + p * outs * a.strideY;
+    emit.strideY = a.strideY;
+    emit.off = y * a.ldy + x;
+    emit.kpanel = a.kpanel;
+    emit.split = a.split;
+    emit.vec = FAST || a.vstore != 0;
+    emit.avail = FAST ? VEC : a.cols_out - x;
+    if (y >= a.nb || avail_in <= 0) {  // padding only: zero outputs of the node's subtree
+      Tc z[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) z[v] = (Tc)0;
+      for (int64_t q = (int64_t)tp * R * R; q < (int64_t)(tp + 1) * R * R; ++q) emit(q, z);
+      continue;
+    }
+    const Tin* X = static_cast<const Tin*>(a.X) + p * a.strideX;
+    const bool full = FAST || (a.vload && avail_in >= VEC);
+    Tc c1[NS], c2[NS];
+    load_coefs<Tc, N0>(c1, coef + ((size_t)(R + 1) * R + (TOP == 1 ? tp : tp / R)) * NS);
+    if constexpr (TOP == 2) load_coefs<Tc, N0>(c2, coef + ((size_t)(R + 2) * R + tp % R) * NS);
+    Tc cin[WC * WC][VEC];
+#pragma unroll
+    for (int e = 0; e < WC * WC; ++e)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) cin[e][v] = (Tc)0;
+    // quadrant (k, l) of the parent, and with TOP = 2 quadrant (k2, l2) inside it; a rolled
+    // loop (16 vector loads in flight per term) keeps the register count of the two-level walk
+#pragma unroll 1
+    for (int kl = 0; kl < (TOP == 1 ? 4 : 16); ++kl) {
+      const int k = TOP == 1 ? kl >> 1 : kl >> 3, l = TOP == 1 ? kl & 1 : (kl >> 2) & 1;
+      const int k2 = TOP == 1 ? 0 : (kl >> 1) & 1, l2 = TOP == 1 ? 0 : kl & 1;
+      const Tc cf = TOP == 1 ? c1[k * 2 + l] : c1[k * 2 + l] * c2[k2 * 2 + l2];
+      if (cf == (Tc)0) continue;
+      const int rb = TOP == 1 ? k * WC : k * 2 * WC + k2 * WC, cb = TOP == 1 ? l * WC : l * 2 * WC + l2 * WC;
+#pragma unroll
+      for (int u = 0; u < WC; ++u)
+#pragma unroll
+        for (int w = 0; w < WC; ++w) {
+          const Tin* src = X + ((rb + u) * a.nb + y) * a.ldx + (cb + w) * colstep + xsrc;
+          Tin raw[VEC];
+          if (full) {
+            load_vec<Tin, VEC>(raw, src);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) raw[v] = (v < avail_in) ? src[v] : (Tin)0;
+          }
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) cin[u * WC + w][v] = cin[u * WC + w][v] + cf * (Tc)raw[v];
+        }
+    }
+    // compact rows 0 (the node) and 1..R (its children) are the local ids of a two-level walk
+    EncodeWalk<Tc, N0, 2, VEC>::go(coef, R, 0, 0, tp, cin, emit);
   }
 }
 
@@ -1242,6 +1354,31 @@ cudaError_t enc_one(const Tables<Tc>& t, const PassArgs& a_in, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+// Passes of TOP + 2 levels for n0 = 2 in fp32 (encode_top_kernel): four positions per thread, as
+// in the two-level pass.
+template <typename Tin, int S, int TOP>
+cudaError_t enc_top(const Tables<float>& t, const PassArgs& a_in, cudaStream_t st) {
+  using Tout = typename StoreType<S>::T;
+  constexpr int N0 = 2, VEC = Vec<float, 2, 2>::value;
+  if (a_in.trans || t.R > kTop3MaxR) return cudaErrorInvalidValue;
+  PassArgs a = a_in;
+  if (a.seg <= 0 || a.seg % 4 || a.mval <= 0 || a.mval > a.seg) return cudaErrorInvalidValue;
+  const int RT = TOP == 1 ? t.R : t.R * t.R;
+  const size_t smem = (size_t)top_rows(t.R, TOP) * t.R * coef_stride(N0) * sizeof(float);
+  const bool xalign = a.plain ? (a.nb % VEC == 0 && (a.mval % VEC == 0 || a.cols_out <= a.seg)) : a.xcol % VEC == 0;
+  a.vload = xalign && a.ldx % VEC == 0 && a.strideX % VEC == 0 && aligned(a.X, VEC * sizeof(Tin));
+  a.vstore = a.ldy % VEC == 0 && a.strideY % VEC == 0 && a.kpanel % VEC == 0 && aligned(a.Y, VEC * sizeof(Tout));
+  const bool fast = a.vload && a.vstore && a.cols_out % VEC == 0 && (a.plain ? a.mval % VEC == 0 : true);
+  dim3 grid = pass_grid(a.rows_out, a.cols_out, a.parents, VEC);
+  if ((uint64_t)grid.x * (uint64_t)RT > 0x7fffffffull) return cudaErrorInvalidValue;
+  grid.x *= (unsigned)RT;
+  auto kern = fast ? encode_top_kernel<Tin, float, S, TOP, VEC, true> : encode_top_kernel<Tin, float, S, TOP, VEC, false>;
+  cudaError_t e = prep(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreadsX, smem, st>>>(t, a);
+  return cudaGetLastError();
+}
+
 template <typename Tin, typename Tc, int S, int N0>
 cudaError_t enc_g(const Tables<Tc>& t, const PassArgs& a, int g, cudaStream_t st) {
   switch (g) {
@@ -1250,7 +1387,10 @@ cudaError_t enc_g(const Tables<Tc>& t, const PassArgs& a, int g, cudaStream_t st
       if constexpr (N0 <= 3) return enc_one<Tin, Tc, S, N0, 2>(t, a, st);
       break;
     case 3:
-      if constexpr (N0 == 2) return enc_one<Tin, Tc, S, N0, 3>(t, a, st);
+      if constexpr (N0 == 2 && std::is_same_v<Tc, float>) return enc_top<Tin, S, 1>(t, a, st);
+      break;
+    case 4:
+      if constexpr (N0 == 2 && std::is_same_v<Tc, float>) return enc_top<Tin, S, 2>(t, a, st);
       break;
   }
   return cudaErrorInvalidValue;
@@ -1372,10 +1512,11 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 
 }  // namespace
 
-// Levels per pass: two for n0 = 2 (16 values per position); one for n0 = 3 and 4.  Passes
-// holding 64 or more values per position (three levels of n0 = 2, two of n0 = 3) need about
-// 220 registers, run at low occupancy, and measured slower than an extra pass over an
-// intermediate.
+// Levels per pass of the register walks: two for n0 = 2 (16 values per position); one for
+// n0 = 3 and 4.  Walks holding 64 or more values per position (three levels of n0 = 2, two of
+// n0 = 3) need about 220 registers, run at low occupancy, and measured slower than an extra
+// pass over an intermediate; the deeper fp32 encodes below split their top levels over CTAs or
+// hand them over in shared memory instead.
 int max_levels_per_pass(int n0) { return n0 == 2 ? 2 : 1; }
 int max_decode_levels_per_pass(int n0, int formula, int64_t m) {
   // Laderman's formula: two levels (the lower handed over in shared memory), when the child rows
@@ -1384,10 +1525,13 @@ int max_decode_levels_per_pass(int n0, int formula, int64_t m) {
   return max_levels_per_pass(n0);
 }
 
-int max_encode_levels_per_pass(int n0, int formula, int64_t m) {
+int max_encode_levels_per_pass(int n0, int R, int formula, int64_t m, int store) {
   // Laderman's formula: two levels (the first in shared memory), when the leaf rows fill the
   // 128-position tiles reasonably (m >= 32)
   if (formula == kFormulaLaderman && m >= 32) return 2;
+  // n0 = 2: four levels, the first two split over the CTAs (encode_top_kernel), for up to
+  // kTop3MaxR children; not for the transposed final pass of tf32 leaves
+  if (n0 == 2 && R <= kTop3MaxR && store != kStoreTF32) return 4;
   return max_levels_per_pass(n0);
 }
 

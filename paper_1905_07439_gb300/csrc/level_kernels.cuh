@@ -60,9 +60,13 @@ struct PassArgs {
 };
 
 int max_levels_per_pass(int n0);
-// Levels an fp32 encode pass covers for leaf size m: two for Laderman's formula when m >= 32
-// (the first level held in shared memory, 128-position tiles), else max_levels_per_pass.
-int max_encode_levels_per_pass(int n0, int formula, int64_t m);
+// Children per node up to which an fp32 n0 = 2 encode pass covers three levels.
+constexpr int kTop3MaxR = 8;
+// Levels an fp32 encode pass covers for leaf size m, R children per node and leaf store type:
+// two for Laderman's formula when m >= 32 (the first level held in shared memory,
+// 128-position tiles); three for n0 = 2 with R <= kTop3MaxR unless the leaves are stored
+// transposed (tf32); else max_levels_per_pass.
+int max_encode_levels_per_pass(int n0, int R, int formula, int64_t m, int store);
 // Levels an fp32 decode pass covers for leaf size m: two for Laderman's formula when m >= 32 (the
 // lower level handed over in shared memory, 64-position tiles), else max_levels_per_pass.
 int max_decode_levels_per_pass(int n0, int formula, int64_t m);

@@ -104,7 +104,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   }
   lo->K = lo->mp * (1 + lo->split);
   lo->seg = seg_pitch(lo->m);
-  lo->passes = plan_passes(L, io == RBC_IO_F32 ? max_encode_levels_per_pass(n0, p->builtin, lo->m) : max_levels_per_pass(n0));
+  lo->passes = plan_passes(L, io == RBC_IO_F32 ? max_encode_levels_per_pass(n0, R, p->builtin, lo->m, lo->store) : max_levels_per_pass(n0));
   lo->dpasses = plan_passes(L, io == RBC_IO_F32 ? max_decode_levels_per_pass(n0, p->builtin, lo->m) : max_levels_per_pass(n0));
   const bool fused_ok = p->scope == RBC_DRAW_PER_LEVEL || p->draw_count <= kMaxDraws;
   if (decode_req == 1 && !fused_ok) return fail(RBC_EUNSUPPORTED, "fused decode needs <= 1024 draw sets");

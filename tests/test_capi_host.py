@@ -118,12 +118,18 @@ def test_workspace_sizes(rbc):
     # staged decode adds the 49 leaf products
     assert fused >= 4 * 2 * 49 * 1024**2
     assert staged - fused >= 4 * 49 * 1024**2
-    # four levels of Strassen run as two passes of two levels: one intermediate level (49
-    # blocks of 2048^2 fp32 per operand) and the bf16 leaves; beyond them only the 256-byte
-    # status word and alignment
+    # four levels of Strassen run as one pass (the first two levels split over the CTAs): no
+    # intermediate, only the bf16 leaves; beyond them only the 256-byte status word and
+    # alignment.  Five levels add a one-level pass before it: one intermediate level (7 blocks
+    # of 4096^2 fp32 per operand at N = 8192)
     p4 = rbc.Plan(U, V, W, levels=4)
     ws4 = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
-    body = 2 * 4 * 49 * 2048**2 + 2 * 2 * 2401 * 512**2
+    body = 2 * 2 * 2401 * 512**2
+    assert body <= ws4 <= body + 4096
+    p5 = rbc.Plan(U, V, W, levels=5, draw_scope=rbc.DRAW_PER_LEVEL)  # fused decode: few draw sets
+    ws5 = p5.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
+    body5 = 2 * 4 * 7 * 4096**2 + 2 * 2 * 16807 * 256**2
+    assert body5 <= ws5 <= body5 + 4096
     assert body <= ws4 <= body + 4096
     # split leaves store two bf16 panels per operand, bf16x6 three: the leaf operand bytes
     # grow by one and two panels

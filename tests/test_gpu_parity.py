@@ -279,6 +279,43 @@ def test_laderman_two_level_encode(rbc, L, m, scope, leaf):
     assert entrywise(C, ref, A, B, 3, L) <= egate(leaf, 3, L)
 
 
+DEEP_N02 = [
+    # formula, L, m, draw scope: ragged leaves (element loads of the plain input), aligned ones
+    # (vector path), a [1, 4] plan whose second pass chunks its per-node draw sets over launches,
+    # dense perturbed coefficients, and the classical rule (R = 8, the largest R of the pass)
+    ("strassen", 3, 37, o.DRAW_PER_NODE),
+    ("strassen", 4, 21, o.DRAW_PER_NODE),
+    ("strassen", 4, 64, o.DRAW_PER_LEVEL),
+    ("strassen", 5, 12, o.DRAW_PER_NODE),
+    ("noisy-strassen", 3, 40, o.DRAW_PER_NODE),
+    ("noisy-strassen", 4, 17, o.DRAW_PER_LEVEL),
+    ("classical2", 3, 24, o.DRAW_PER_NODE),
+]
+
+
+@pytest.mark.parametrize("name,L,m,scope", DEEP_N02)
+@pytest.mark.parametrize("leaf", ["f32", "bf16x6", "bf16", "tf32"])
+def test_n0_2_deep_encode(rbc, name, L, m, scope, leaf):
+    """fp32 encodes of n0 = 2 formulas with R <= 8 run three- and four-level passes, the first one
+    or two levels split over the CTAs (tf32 leaves keep two-level passes: their last pass
+    writes transposed): against the oracle."""
+    if name == "classical2":
+        from rbc_inputs.formulas import classical_formula
+        U, V, W = classical_formula(2)
+    else:
+        U, V, W = formula(name, seed=4)
+    N = 2**L * m
+    A, B = matrix_pair("normal", N, seed=90 + m)
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    seed = 3 * m + L
+    plan = rbc.Plan(U, V, W, levels=L, seed=seed, draw_scope=scope)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, seed, scope=scope))
+    C = gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_NAMES[leaf], 2)
+    assert normwise(C, ref, A, B) <= gate(leaf, 2, L, N)
+    assert entrywise(C, ref, A, B, 2, L) <= egate(leaf, 2, L)
+
+
 def test_workspace_status_word_clear_after_calls(rbc):
     import ctypes
     U, V, W = formula("strassen")
