@@ -33,8 +33,8 @@ pytestmark = pytest.mark.gpu
 SAMPLES = 1024
 
 
-def sample_entries(n, m, seed):
-    """SAMPLES (row, col) pairs: every pairing of the special indices (first, last, both sides of
+def sample_entries(n, m, seed, count=SAMPLES):
+    """count (row, col) pairs: every pairing of the special indices (first, last, both sides of
     leaf boundaries, tile edges inside the first and last leaf block), then uniform ones."""
     q = n // m
     special = {0, n - 1}
@@ -47,9 +47,9 @@ def sample_entries(n, m, seed):
                 special.add(base + t)
     sp = np.array(sorted(special))
     rows, cols = np.meshgrid(sp, sp, indexing="ij")
-    rows, cols = rows.ravel()[:SAMPLES], cols.ravel()[:SAMPLES]
+    rows, cols = rows.ravel()[:count], cols.ravel()[:count]
     rng = np.random.default_rng(seed)
-    extra = SAMPLES - rows.size
+    extra = count - rows.size
     rows = np.concatenate([rows, rng.integers(0, n, extra)])
     cols = np.concatenate([cols, rng.integers(0, n, extra)])
     return rows, cols
@@ -73,7 +73,7 @@ def _bench_inputs(n):
     return A, B
 
 
-def _sampled_normwise(rbc, name, n, L, seed, A, B, leaf, fseed=7, mixed=False):
+def _sampled_normwise(rbc, name, n, L, seed, A, B, leaf, fseed=7, mixed=False, count=SAMPLES):
     """(normwise estimate, n0, relative rms error, max entrywise ratio |dC| / bound) over the
     sampled entries."""
     U, V, W = formula_by_name(name, seed=fseed)
@@ -81,7 +81,7 @@ def _sampled_normwise(rbc, name, n, L, seed, A, B, leaf, fseed=7, mixed=False):
     plan = rbc.Plan(U, V, W, levels=L, seed=seed)
     Ad, Bd = A.cuda(), B.cuda()
     C = rbc.matmul(plan, Ad, Bd, leaf=rbc.LEAF_NAMES[leaf])
-    rows, cols = sample_entries(n, n // n0**L, n + 31 * L)
+    rows, cols = sample_entries(n, n // n0**L, n + 31 * L, count)
     got = C[torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")].double().cpu().numpy()
     del C, Ad, Bd
     torch.cuda.empty_cache()
@@ -102,6 +102,18 @@ SWEEP = [("strassen", 8192, L) for L in (1, 2, 3, 4)] + [("laderman", 6561, L) f
 def test_sweep_sampled_parity(rbc, name, n, L):
     A, B = _bench_inputs(n)
     err, n0, _, ent = _sampled_normwise(rbc, name, n, L, 2024 + L, A, B, "bf16x6")
+    assert err <= gate("bf16x6", n0, L, n), (name, n, L, err)
+    assert ent <= egate("bf16x6", n0, L), (name, n, L, ent)
+
+
+# Deeper plans than the sweep's: Laderman L = 4 (two two-level passes, the second over the 529
+# depth-2 blocks), Strassen L = 5 (a one-level pass, then four-level passes over the 7 depth-1
+# blocks) and perturbed Strassen L = 4 (one four-level pass, dense coefficients); 128 sampled
+# entries each (the oracle's recursion per entry grows as R^L).
+@pytest.mark.parametrize("name,n,L", [("laderman", 2592, 4), ("strassen", 8192, 5), ("noisy-strassen", 4096, 4)])
+def test_deep_plans_sampled_parity(rbc, name, n, L):
+    A, B = _bench_inputs(n)
+    err, n0, _, ent = _sampled_normwise(rbc, name, n, L, 77 + L, A, B, "bf16x6", count=128)
     assert err <= gate("bf16x6", n0, L, n), (name, n, L, err)
     assert ent <= egate("bf16x6", n0, L), (name, n, L, ent)
 
