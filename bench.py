@@ -182,9 +182,9 @@ class ClockSampler:
 # capture describes the kernel it measured only, so another library version reports null.
 LEAF_TRAFFIC_STEP = {("bf16x6", 200): 46_604_675_328}
 # Stored panels per leaf operand and tensor-core products per leaf product of each leaf mode.
-LEAF_PANELS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 2, "3xtf32": 2, "bf16x6": 3}
-LEAF_PRODUCTS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 3, "3xtf32": 3, "bf16x6": 6}
-LEAF_BYTES = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2, "bf16x6": 2}
+LEAF_PANELS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 2, "3xtf32": 2, "bf16x6": 3, "f16x3": 2}
+LEAF_PRODUCTS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 3, "3xtf32": 3, "bf16x6": 6, "f16x3": 3}
+LEAF_BYTES = {"f32": 4, "tf32": 4, "3xtf32": 4, "bf16": 2, "f16": 2, "3xbf16": 2, "bf16x6": 2, "f16x3": 2}
 
 
 def case_flops(n, L, R, n0):
@@ -727,7 +727,7 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
-PRECISION_LEAVES = ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f32"]
+PRECISION_LEAVES = ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f16x3", "f32"]
 
 
 def run_precision(args):

@@ -61,7 +61,17 @@ typedef enum { RBC_IO_F64 = 0, RBC_IO_F32 = 1 } rbc_io_dtype;
  * b1 = round(x - b0), b2 = round(x - b0 - b1); exact for normal fp32 x) and adds the six
  * products whose pieces carry the leading 24 bits, b0*b2' + b2*b0' + b1*b1' + b0*b1' +
  * b1*b0' + b0*b0' (the bf16x6 method of Henry, Tang & Heinecke, 2019): an fp32-accurate
- * product on the bf16 tensor cores. */
+ * product on the bf16 tensor cores.
+ * RBC_LEAF_F16X3 scales every row of the left leaf operands and every column of the right
+ * ones by a power of two (the same for all leaves: from the largest |entry| of the rows of A
+ * congruent mod m, of the columns of B congruent mod m, times the formula's growth bound per
+ * level), so that the scaled entries stay below 2^15, stores two fp16 pieces x = h0 + h1
+ * (h0 = round(x), h1 = round(x - h0), kept as 2^11 h1: 22 significant bits), adds
+ * h0*h1' + h1*h0' and h0*h0' in two accumulators drained every 64 elements of K (the tensor
+ * cores' truncating accumulation of 22-bit products is biased on same-signed data), and removes
+ * the scales in the leaf epilogue (exact powers of two).  Half the tensor-core products of
+ * bf16x6 at about 2^-22 relative representation error; entries 2^29 or more below the largest
+ * of their class lose relative accuracy gradually (fp16 subnormals). */
 typedef enum {
   RBC_LEAF_F64 = 0,    /* fp64 FMA (SIMT); I/O must be F64                         */
   RBC_LEAF_F32 = 1,    /* fp32 FMA (SIMT)                                          */
@@ -70,7 +80,8 @@ typedef enum {
   RBC_LEAF_F16 = 4,    /* tcgen05 kind::f16 with fp16 operands                      */
   RBC_LEAF_3XBF16 = 5, /* three bf16 tcgen05 products (split compensated)          */
   RBC_LEAF_3XTF32 = 6, /* three tf32 tcgen05 products (split compensated)         */
-  RBC_LEAF_BF16X6 = 7  /* six bf16 tcgen05 products of three-piece splits (fp32 level) */
+  RBC_LEAF_BF16X6 = 7, /* six bf16 tcgen05 products of three-piece splits (fp32 level) */
+  RBC_LEAF_F16X3 = 8   /* three fp16 tcgen05 products of scaled two-piece splits      */
 } rbc_leaf_dtype;
 
 /* Which parts of the signed permutations are drawn (Section 3.2: fully randomized,

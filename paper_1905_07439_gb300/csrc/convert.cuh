@@ -10,6 +10,11 @@ namespace rbc {
 
 enum LeafStore : int { kStoreF64 = 0, kStoreF32 = 1, kStoreTF32 = 2, kStoreBF16 = 3, kStoreF16 = 4 };
 
+// The low fp16 piece of a split (f16x3 leaves) is stored multiplied by 2^11, so that it stays a
+// normal fp16 number whenever the high piece is one (the remainder is at most 2^-11 of the
+// value); the leaf kernel scales the cross-term products back by 2^-11.
+constexpr float kF16LoScale = 2048.f;
+
 // Round-to-nearest-even of an fp32 value to 10 explicit significand bits (tf32), kept in
 // an fp32 container with the low 13 bits zero.  Integer arithmetic on the bit pattern;
 // finite inputs only (the caller's data are finite).

@@ -91,6 +91,8 @@ TcGemmArgs inst_args(const rbc_group_s* g, size_t i, char* ws) {
   a.strideM = lo.mstride;
   a.leaf = g->leaf;
   a.status = reinterpret_cast<int*>(ws);
+  a.rinv = leaf_inverse(lo, w, 0);
+  a.cinv = leaf_inverse(lo, w, 1);
   return a;
 }
 
@@ -181,7 +183,8 @@ rbc_status enqueue(rbc_group_s* g, char* ws, cudaStream_t st) {
     const rbc_group_item& it = g->items[i];
     char* w = ws + g->ws_off[i];
     cudaStream_t si = g->side[i % ns];
-    s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 0, it.A, it.lda, w, tab, si);
+    s = leaf_scales(it.plan, g->layouts[i], it.A, it.lda, it.B, it.ldb, it.N, w, si);
+    if (s == RBC_OK) s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 0, it.A, it.lda, w, tab, si);
     if (s == RBC_OK) s = encode_operand<float>(it.plan, g->layouts[i], RBC_IO_F32, 1, it.B, it.ldb, w, tab, si);
     if (s != RBC_OK) return s;
   }
@@ -315,7 +318,7 @@ rbc_status rbc_group_tune(rbc_group_t g, void* workspace, size_t bytes, void* st
   std::vector<Config> cands;
   const bool split = leaf_panels(g->leaf) > 1;
   for (int bn : {128, 256}) {
-    if (bn == 256 && (!g->bn256_ok || g->leaf == RBC_LEAF_BF16X6)) continue;
+    if (bn == 256 && (!g->bn256_ok || g->leaf == RBC_LEAF_BF16X6 || g->leaf == RBC_LEAF_F16X3)) continue;
     for (int ctas : {1, 2}) {
       if (ctas == 2 && (split || bn != 128)) continue;
       for (int grp : {0, 1, 8}) cands.push_back(Config{bn, grp, ctas});
@@ -380,7 +383,8 @@ rbc_status rbc_group_configure(rbc_group_t g, const rbc_group_tuning* cfg) {
   const bool split = leaf_panels(g->leaf) > 1;
   if (cfg->bn != 128 && cfg->bn != 256) return fail(RBC_EINVAL, "bn must be 128 or 256");
   if (cfg->bn == 256 && !g->bn256_ok) return fail(RBC_EINVAL, "bn 256 needs padded leaf sizes divisible by 256");
-  if (cfg->bn == 256 && g->leaf == RBC_LEAF_BF16X6) return fail(RBC_EINVAL, "bf16x6 leaves take bn 128");
+  if (cfg->bn == 256 && (g->leaf == RBC_LEAF_BF16X6 || g->leaf == RBC_LEAF_F16X3))
+    return fail(RBC_EINVAL, "bf16x6 and f16x3 leaves take bn 128");
   const int grp = cfg->group;
   if (grp != 0 && grp != 1 && grp != 2 && grp != 4 && grp != 8 && grp != 16)
     return fail(RBC_EINVAL, "group must be 0, 1, 2, 4, 8 or 16");

@@ -263,7 +263,22 @@ struct EncodeEmitV {
   int64_t strideY, off, kpanel, avail;
   int split;
   bool vec;
-  __device__ __forceinline__ void operator()(int64_t path, const Tc (&val)[VEC]) {
+  bool scaled = false;  // f16x3 leaves: multiply by sc (powers of two) before the split
+  Tc sc[VEC];
+  // Leaf operand scale of positions (y, x .. x + VEC - 1) of the last encode pass.
+  __device__ __forceinline__ void set_scale(const PassArgs& a, int64_t y, int64_t x) {
+    if (!a.lscale) return;
+    scaled = true;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      const int64_t i = a.tensor == 0 ? y : min(x + v, a.cols_out - 1);
+      sc[v] = (Tc)a.lscale[i];
+    }
+  }
+  __device__ __forceinline__ void operator()(int64_t path, const Tc (&val_in)[VEC]) {
+    Tc val[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) val[v] = scaled ? val_in[v] * sc[v] : val_in[v];
     Tout* dst = Y + path * strideY + off;
     if constexpr ((S == kStoreBF16 || S == kStoreF16) && sizeof(Tc) == 4 && VEC % 2 == 0) {
       using P = Pair2<S>;
@@ -284,11 +299,14 @@ struct EncodeEmitV {
           const float2 h = P::back(h2[i]);
           rem[2 * i] = val[2 * i] - h.x;
           rem[2 * i + 1] = val[2 * i + 1] - h.y;
-          l2[i] = P::cvt(rem[2 * i], rem[2 * i + 1]);
+          if constexpr (S == kStoreF16)  // f16x3: the low piece is kept as 2^11 (x - h0)
+            l2[i] = P::cvt(kF16LoScale * rem[2 * i], kF16LoScale * rem[2 * i + 1]);
+          else
+            l2[i] = P::cvt(rem[2 * i], rem[2 * i + 1]);
         }
         memcpy(lo, l2, sizeof(lo));
         store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
-        if (split > 1) {
+        if (S != kStoreF16 && split > 1) {
           typename P::T t2[VEC / 2];
           Tout lo2[VEC];
 #pragma unroll
@@ -311,10 +329,10 @@ struct EncodeEmitV {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           rem[v] = val[v] - (Tc)from_store<S>(hi[v]);
-          lo[v] = to_store<S>((double)rem[v]);
+          lo[v] = to_store<S>(S == kStoreF16 ? (double)kF16LoScale * (double)rem[v] : (double)rem[v]);
         }
         store_some<Tout, VEC>(dst + kpanel, lo, vec, avail);
-        if (split > 1) {
+        if (S != kStoreF16 && split > 1) {
 #pragma unroll
           for (int v = 0; v < VEC; ++v) lo[v] = to_store<S>((double)(rem[v] - (Tc)from_store<S>(lo[v])));
           store_some<Tout, VEC>(dst + 2 * kpanel, lo, vec, avail);
@@ -366,6 +384,7 @@ __global__ void __launch_bounds__(kThreadsX) encode_pass_kernel(const __grid_con
     emit.split = a.split;
     emit.vec = FAST || a.vstore != 0;
     emit.avail = FAST ? VEC : a.cols_out - x;
+    emit.set_scale(a, y, x);
     if (y >= a.nb || avail_in <= 0) {  // padding only: zero outputs
       Tc z[VEC];
 #pragma unroll
@@ -449,6 +468,7 @@ __global__ void __launch_bounds__(kThreadsX) encode_top_kernel(const __grid_cons
     emit.split = a.split;
     emit.vec = FAST || a.vstore != 0;
     emit.avail = FAST ? VEC : a.cols_out - x;
+    emit.set_scale(a, y, x);
     if (y >= a.nb || avail_in <= 0) {  // padding only: zero outputs of the node's subtree
       Tc z[VEC];
 #pragma unroll
@@ -892,6 +912,7 @@ __global__ void __launch_bounds__(kThreadsX) encode_fixed_kernel(const __grid_co
     emit.split = a.split;
     emit.vec = FAST || a.vstore != 0;
     emit.avail = FAST ? VEC : a.cols_out - x;
+    emit.set_scale(a, y, x);
     if (padding) {  // zero outputs
       Tc z[VEC];
 #pragma unroll
@@ -1058,6 +1079,7 @@ __global__ void __launch_bounds__(F::n0 * F::n0 * (kDeepPos / 4))
       e.split = a.split;
       e.vec = a.vstore != 0;
       e.avail = a.cols_out - x;
+      e.set_scale(a, y, x);
       return e;
     };
     if (y >= a.nb) {  // a padding row of every output: zeros
@@ -1497,13 +1519,18 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
   if (y >= a.rows_out) return;
   const Tin* X = static_cast<const Tin*>(a.X);
   const int64_t sy = a.trans ? x : y, sx = a.trans ? y : x;  // source entry
-  const double v = (sy < a.nb && sx < a.nb) ? (double)X[sy * a.ldx + sx] : 0.0;
+  double v = (sy < a.nb && sx < a.nb) ? (double)X[sy * a.ldx + sx] : 0.0;
+  if (a.lscale) v *= (double)a.lscale[a.tensor == 0 ? y : x];  // f16x3: a power of two, exact
   Tout* dst = static_cast<Tout*>(a.Y) + y * a.ldy + x;
   const Tout hi = to_store<S>(v);
   dst[0] = hi;
   if (a.split) {
     // v holds an fp32 value: the remainders below are exact
     const double rem = v - from_store<S>(hi);
+    if (S == kStoreF16) {  // f16x3: the low piece is kept as 2^11 (x - h0)
+      dst[a.kpanel] = to_store<S>((double)kF16LoScale * rem);
+      return;
+    }
     const Tout lo = to_store<S>(rem);
     dst[a.kpanel] = lo;
     if (a.split > 1) dst[2 * a.kpanel] = to_store<S>(rem - from_store<S>(lo));
@@ -1511,6 +1538,74 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 }
 
 }  // namespace
+
+namespace {
+
+// ------------------------------------------------------------------ f16x3 leaf operand scales
+// Largest |entry| of each class of rows (rows = 1: rows i == r mod m, over all columns) or of
+// columns (rows = 0: columns j == c mod m, over all rows) of an N x N fp32 matrix, as fp32 bit
+// patterns (non-negative floats order like their bits) gathered with atomicMax.  A CTA covers
+// 32 rows x 1024 columns: each warp reads whole 128-byte row segments.
+constexpr int kAmaxRows = 32, kAmaxCols = 1024;
+__global__ void __launch_bounds__(256) fold_absmax_kernel(const float* __restrict__ X, int64_t N, int64_t ld,
+                                                          int64_t m, int rows, unsigned* __restrict__ amax) {
+  const int64_t r0 = (int64_t)blockIdx.y * kAmaxRows, c0 = (int64_t)blockIdx.x * kAmaxCols;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (rows) {
+    // warp w: rows r0 + w, r0 + w + 8, ...; lanes stride the columns
+    for (int rr = warp; rr < kAmaxRows; rr += 8) {
+      const int64_t r = r0 + rr;
+      if (r >= N) break;
+      float mx = 0.f;
+      for (int64_t c = c0 + lane; c < c0 + kAmaxCols && c < N; c += 32) mx = fmaxf(mx, fabsf(X[r * ld + c]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > 0.f) atomicMax(amax + r % m, __float_as_uint(mx));
+    }
+  } else {
+    // thread t: columns c0 + t, c0 + t + 256, ... over the CTA's rows
+    for (int64_t c = c0 + threadIdx.x; c < c0 + kAmaxCols && c < N; c += 256) {
+      float mx = 0.f;
+      for (int64_t r = r0; r < r0 + kAmaxRows && r < N; ++r) mx = fmaxf(mx, fabsf(X[r * ld + c]));
+      if (mx > 0.f) atomicMax(amax + c % m, __float_as_uint(mx));
+    }
+  }
+}
+
+__global__ void leaf_scales_kernel(const unsigned* __restrict__ amax, int64_t m, int64_t mp, float growth,
+                                   float* __restrict__ scale, float* __restrict__ inv) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= mp) return;
+  int e = 0;
+  if (r < m) {
+    const float t = __uint_as_float(amax[r]) * growth;
+    if (t > 0.f && t <= 3.0e38f) {
+      int ex;
+      frexpf(t, &ex);  // t < 2^ex
+      e = min(max(15 - ex, -120), 120);
+    }
+  }
+  scale[r] = ldexpf(1.f, e);
+  inv[r] = ldexpf(1.f, -e);
+}
+
+}  // namespace
+
+cudaError_t launch_fold_absmax(const float* X, int64_t N, int64_t ld, int64_t m, int rows, unsigned* amax,
+                               cudaStream_t st) {
+  if (N <= 0 || m <= 0 || ld < N) return cudaErrorInvalidValue;
+  const int64_t gy = (N + kAmaxRows - 1) / kAmaxRows, gx = (N + kAmaxCols - 1) / kAmaxCols;
+  if (gy > 65535) return cudaErrorInvalidValue;
+  fold_absmax_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(X, N, ld, m, rows, amax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, float growth, float* scale, float* inv,
+                               cudaStream_t st) {
+  if (mp <= 0 || m > mp) return cudaErrorInvalidValue;
+  leaf_scales_kernel<<<(unsigned)((mp + 255) / 256), 256, 0, st>>>(amax, m, mp, growth, scale, inv);
+  return cudaGetLastError();
+}
 
 // Levels per pass of the register walks: two for n0 = 2 (16 values per position); one for
 // n0 = 3 and 4.  Walks holding 64 or more values per position (three levels of n0 = 2, two of

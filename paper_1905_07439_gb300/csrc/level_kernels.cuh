@@ -55,6 +55,9 @@ struct PassArgs {
   int vload;      // set by the launcher: input rows allow VEC-wide vector loads
   int vstore;     // set by the launcher: output rows allow VEC-wide vector stores
   int64_t kpanel;
+  // encode, last pass of f16x3 leaves: power-of-two factor per leaf row (tensor 0: output row y)
+  // or leaf column (tensor 1: output column x) applied before the split; null: none
+  const float* lscale;
   int64_t dbase[kMaxLevels];
   int64_t dfirst[kMaxLevels];
 };
@@ -77,6 +80,16 @@ cudaError_t launch_encode_pass(const Tables<float>& t, const PassArgs& a, int n0
                                cudaStream_t st);
 cudaError_t launch_decode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, cudaStream_t st);
 cudaError_t launch_decode_pass(const Tables<float>& t, const PassArgs& a, int n0, int g, cudaStream_t st);
+
+// Leaf operand scales of the f16x3 mode.  amax[0 .. m) (zeroed by the caller) receives, as
+// fp32 bit patterns, max |X[i][c]| over the rows i == r (mod m) of X (rows = 1) or max |X[r][j]|
+// over the columns j == c (mod m) (rows = 0); one launch.
+cudaError_t launch_fold_absmax(const float* X, int64_t N, int64_t ld, int64_t m, int rows, unsigned* amax,
+                               cudaStream_t st);
+// scale[r] = 2^e with e the largest integer such that amax[r] * growth * 2^e <= 2^15 (1 for a
+// zero class or r >= m), inv[r] = 2^-e, for r < mp.
+cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, float growth, float* scale, float* inv,
+                               cudaStream_t st);
 
 // Batched leaf products M_leaf = S_leaf * T_leaf on the CUDA cores (fp32 or fp64 FMA).
 struct SimtGemmArgs {

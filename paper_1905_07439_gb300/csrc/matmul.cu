@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <memory>
 #include <vector>
 
@@ -22,12 +23,12 @@ thread_local int64_t g_launches = 0;  // kernels launched by the current call
 
 bool is_tc_leaf(int leaf) {
   return leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_BF16 || leaf == RBC_LEAF_F16 ||
-         leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_BF16X6;
+         leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_BF16X6 || leaf == RBC_LEAF_F16X3;
 }
 
 int leaf_panels(int leaf) {
   if (leaf == RBC_LEAF_BF16X6) return 3;
-  return (leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32) ? 2 : 1;
+  return (leaf == RBC_LEAF_3XBF16 || leaf == RBC_LEAF_3XTF32 || leaf == RBC_LEAF_F16X3) ? 2 : 1;
 }
 
 int leaf_store(int leaf) {
@@ -39,7 +40,8 @@ int leaf_store(int leaf) {
     case RBC_LEAF_BF16:
     case RBC_LEAF_3XBF16:
     case RBC_LEAF_BF16X6: return kStoreBF16;
-    case RBC_LEAF_F16: return kStoreF16;
+    case RBC_LEAF_F16:
+    case RBC_LEAF_F16X3: return kStoreF16;
   }
   return -1;
 }
@@ -76,7 +78,7 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
   if (reals > 1 && (p->L == 0 || decode_req != 2))
     return fail(RBC_EINVAL, "realization batches need L >= 1 and staged decode");
   if (io != RBC_IO_F32 && io != RBC_IO_F64) return fail(RBC_EINVAL, "bad io dtype");
-  if (leaf < RBC_LEAF_F64 || leaf > RBC_LEAF_BF16X6) return fail(RBC_EINVAL, "bad leaf dtype");
+  if (leaf < RBC_LEAF_F64 || leaf > RBC_LEAF_F16X3) return fail(RBC_EINVAL, "bad leaf dtype");
   if (io == RBC_IO_F64 && leaf != RBC_LEAF_F64)
     return fail(RBC_EUNSUPPORTED, "fp64 I/O supports the fp64 leaf mode only");
   if (io == RBC_IO_F32 && leaf == RBC_LEAF_F64)
@@ -127,6 +129,10 @@ rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int dec
     off += bytes;
     lo->encB[d] = off;
     off += bytes;
+  }
+  if (leaf == RBC_LEAF_F16X3) {  // leaf operand scales: amax S, T (bits), scale S, T, inverse S, T
+    lo->scales = off;
+    off += align256(6 * (size_t)lo->mp * sizeof(float));
   }
   const int64_t leaves = reals * ipow(R, L);
   const size_t leaf_bytes = align256((size_t)leaves * lo->mp * lo->K * lo->es_leaf);
@@ -237,6 +243,48 @@ rbc_status launch_tables(const Reals& rs, int d, int g, int64_t k0, int64_t kc, 
   return RBC_OK;
 }
 
+// f16x3 leaf operand scales in the workspace: [amax S | amax T | scale S | scale T | inverse S |
+// inverse T], mp entries each.
+const float* leaf_scale(const Layout& lo, char* ws, int tensor) {
+  return lo.scales ? reinterpret_cast<const float*>(ws + lo.scales) + (2 + tensor) * lo.mp : nullptr;
+}
+const float* leaf_inverse(const Layout& lo, char* ws, int tensor) {
+  return lo.scales ? reinterpret_cast<const float*>(ws + lo.scales) + (4 + tensor) * lo.mp : nullptr;
+}
+
+// Growth bound of the leaf operand entries over the recursion: (max_r sum_{k,l} |u_klr|)^L for
+// the left operand (V for the right); the signed permutations keep each column's magnitudes.
+double leaf_growth(const rbc_plan_s* p, int tensor) {
+  const std::vector<double>& X = tensor == 0 ? p->U : p->V;
+  double g = 0;
+  for (int r = 0; r < p->R; ++r) {
+    double c = 0;
+    for (int e = 0; e < p->n0 * p->n0; ++e) c += std::fabs(X[(size_t)e * p->R + r]);
+    g = std::max(g, c);
+  }
+  double t = 1;
+  for (int d = 0; d < p->L; ++d) t *= g;
+  return t;
+}
+
+// The f16x3 scales of one call: the largest |entry| of each class of rows of A and of columns of
+// B congruent mod m (the rows of S and columns of T they feed), then the power of two per class
+// that keeps the grown entries below 2^15.
+rbc_status leaf_scales(const rbc_plan_s* p, const Layout& lo, const void* A, int64_t lda, const void* B,
+                       int64_t ldb, int64_t N, char* ws, cudaStream_t st) {
+  if (!lo.scales) return RBC_OK;
+  unsigned* amax = reinterpret_cast<unsigned*>(ws + lo.scales);
+  float* f = reinterpret_cast<float*>(ws + lo.scales);
+  cudaError_t e = cudaMemsetAsync(amax, 0, 2 * (size_t)lo.mp * sizeof(unsigned), st);
+  if (e == cudaSuccess) e = launch_fold_absmax(static_cast<const float*>(A), N, lda, lo.m, 1, amax, st);
+  if (e == cudaSuccess) e = launch_fold_absmax(static_cast<const float*>(B), N, ldb, lo.m, 0, amax + lo.mp, st);
+  for (int tensor = 0; tensor < 2 && e == cudaSuccess; ++tensor)
+    e = launch_leaf_scales(amax + tensor * lo.mp, lo.m, lo.mp, (float)std::min(leaf_growth(p, tensor), 1e30),
+                           f + (2 + tensor) * lo.mp, f + (4 + tensor) * lo.mp, st);
+  g_launches += 4;
+  return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
+}
+
 // Encode one operand through all passes into the leaf operand buffer (row-major, K-major
 // rows of length lo.K, zero padded to mp, split panels [hi | lo]).
 template <typename T>
@@ -263,6 +311,8 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
     a.seg = lo.mp;
     a.mval = lo.m;
     a.plain = 1;
+    a.tensor = tensor;
+    a.lscale = leaf_scale(lo, ws, tensor);
     cudaError_t e = launch_encode_pass(tab, a, n0, 0, io, lo.store, st);
     ++g_launches;
     return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
@@ -302,6 +352,7 @@ rbc_status encode_operand(const Reals& rs, const Layout& lo, int io, int tensor,
         a.seg = lo.mp;  // one segment per leaf row
         // tf32 tensor-core leaves take T K-major: write T^T
         a.trans = tensor == 1 && lo.store == kStoreTF32;
+        a.lscale = leaf_scale(lo, ws, tensor);
       } else {
         a.Y = ws + enc[d + g] + (size_t)first * outs * nb * w_nb * lo.es_io;
         a.ldy = w_nb;
@@ -388,7 +439,13 @@ rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, 
   Tables<T>& tab = *box.t;
   const rbc_plan_s* p = rs.plan;
   mark(opts, 0, st);
-  rbc_status s = encode_operand<T>(rs, lo, io, 0, A, lda, ws, tab, st);
+  rbc_status s = RBC_OK;
+  if (lo.scales) {
+    if constexpr (sizeof(T) != 4) return fail(RBC_EUNSUPPORTED, "f16x3 leaves need fp32 I/O");
+    s = leaf_scales(p, lo, A, lda, B, ldb, N, ws, st);
+    if (s != RBC_OK) return s;
+  }
+  s = encode_operand<T>(rs, lo, io, 0, A, lda, ws, tab, st);
   if (s != RBC_OK) return s;
   s = encode_operand<T>(rs, lo, io, 1, B, ldb, ws, tab, st);
   if (s != RBC_OK) return s;
@@ -423,6 +480,8 @@ rbc_status run(const Reals& rs, const Layout& lo, const void* A, const void* B, 
     g.leaf = leaf;
     g.status = reinterpret_cast<int*>(ws);
     g.stall = opts ? opts->stall_leaf_copies : 0;
+    g.rinv = leaf_inverse(lo, ws, 0);
+    g.cinv = leaf_inverse(lo, ws, 1);
     if constexpr (sizeof(T) == 4) {
       cudaError_t e = launch_tc_gemm(tab, g, st);
       ++g_launches;

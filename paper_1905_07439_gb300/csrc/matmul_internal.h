@@ -39,6 +39,7 @@ struct Layout {
   Passes dpasses;  // decode passes (the same levels may be grouped differently)
   size_t encA[kMaxLevels + 1] = {}, encB[kMaxLevels + 1] = {};  // intermediates at depth d
   size_t leafS = 0, leafT = 0, M = 0, dec[kMaxLevels + 1] = {};
+  size_t scales = 0;    // f16x3: leaf operand scales (0: none)
   int64_t mstride = 0;  // elements from one leaf product to the next in M (mp^2)
   size_t total = 0;
 };
@@ -55,7 +56,15 @@ struct Reals {
 };
 
 bool is_tc_leaf(int leaf);
-int leaf_panels(int leaf);  // stored panels per leaf operand: 1, 2 (split modes) or 3 (bf16x6)
+int leaf_panels(int leaf);  // stored panels per leaf operand: 1, 2 (split modes, f16x3) or 3 (bf16x6)
+// f16x3 leaf operand scales of a layout (null for other modes): scale (encode) and inverse
+// (leaf epilogue) of the rows of S (tensor 0) or the columns of T (tensor 1), in workspace ws.
+const float* leaf_scale(const Layout& lo, char* ws, int tensor);
+const float* leaf_inverse(const Layout& lo, char* ws, int tensor);
+// Compute the f16x3 scales of one product (A, B: N x N fp32, device) into ws; RBC_OK when the
+// layout has none.
+rbc_status leaf_scales(const rbc_plan_s* p, const Layout& lo, const void* A, int64_t lda, const void* B,
+                       int64_t ldb, int64_t N, char* ws, cudaStream_t st);
 Passes plan_passes(int L, int g);  // passes of at most g levels
 // reals > 1: the layout of that many realizations (staged decode only).
 rbc_status make_layout(const rbc_plan_s* p, int64_t N, int io, int leaf, int decode_req, Layout* lo,

@@ -162,7 +162,7 @@ rbc_status enqueue_grouped(rbc_queue_s* q, Unit& u, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ws0, 0, sizeof(int), st);  // the unit's status word
   if (e != cudaSuccess) return fail(RBC_ECUDA, cudaGetErrorString(e));
   // instance descriptors: tile widths and CTAs per SM as a single product of this mode takes them
-  bool all256 = u.leaf != RBC_LEAF_BF16X6, small = leaf_panels(u.leaf) == 1;
+  bool all256 = u.leaf != RBC_LEAF_BF16X6 && u.leaf != RBC_LEAF_F16X3, small = leaf_panels(u.leaf) == 1;
   for (size_t i = 0; i < n; ++i) {
     all256 = all256 && lo[i].mp % 256 == 0;
     small = small && lo[i].mp <= 256;
@@ -192,6 +192,8 @@ rbc_status enqueue_grouped(rbc_queue_s* q, Unit& u, cudaStream_t st) {
     a.strideM = lo[i].mstride;
     a.leaf = u.leaf;
     a.status = reinterpret_cast<int*>(ws0);
+    a.rinv = leaf_inverse(lo[i], w, 0);
+    a.cinv = leaf_inverse(lo[i], w, 1);
     if (!tc_prepare_instance(a, bn, tc_default_group(u.leaf, a.mp, a.K), tiles, &insts[i], &maps[2 * i]))
       return fail(RBC_EINVAL, "grouped unit: tensor map or tile shape rejected");
     tiles += tc_instance_tiles(insts[i]);
@@ -199,7 +201,8 @@ rbc_status enqueue_grouped(rbc_queue_s* q, Unit& u, cudaStream_t st) {
   for (size_t i = 0; i < n; ++i) {
     const rbc_request& r = u.jobs[i].req;
     char* w = q->pool.base() + u.offs[i];
-    rbc_status s = encode_operand<float>(r.plan, lo[i], RBC_IO_F32, 0, r.A, r.lda, w, *tab, st);
+    rbc_status s = leaf_scales(r.plan, lo[i], r.A, r.lda, r.B, r.ldb, r.N, w, st);
+    if (s == RBC_OK) s = encode_operand<float>(r.plan, lo[i], RBC_IO_F32, 0, r.A, r.lda, w, *tab, st);
     if (s == RBC_OK) s = encode_operand<float>(r.plan, lo[i], RBC_IO_F32, 1, r.B, r.ldb, w, *tab, st);
     if (s != RBC_OK) return s;
   }

@@ -20,9 +20,12 @@
 // Split-compensated modes keep hi and lo panels of each operand in a stage and issue
 // hi*lo' + lo*hi' + hi*hi' per K step into the same accumulator; the bf16x6 mode keeps three
 // panels b0, b1, b2 per operand and issues b0*b2' + b2*b0' + b1*b1' + b0*b1' + b1*b0' +
-// b0*b0' (smallest terms first).  Tiles are 256 wide whenever the padded leaf size allows it
-// (a stage then holds 48 KB per panel set: four stages plain, two split), else 128 wide (six
-// stages plain, three split); bf16x6 tiles are 128 wide with two stages of 96 KB.
+// b0*b0' (smallest terms first); the f16x3 mode keeps two scaled fp16 panels h0, h1 and issues
+// h0*h1' + h1*h0' into a cross-term accumulator and h0*h0' into a main one, and its epilogue
+// multiplies each entry by the inverse row and column scales.  Tiles are 256 wide whenever the
+// padded leaf size allows it (a stage then holds 48 KB per panel set: four stages plain, two
+// split), else 128 wide (six stages plain, three split); bf16x6 tiles are 128 wide with two
+// stages of 96 KB, f16x3 tiles 128 wide with three stages of 64 KB.
 // Every mbarrier wait is bounded (2 s); on expiry the kernel records RBC_ETIMEOUT in the
 // workspace status word, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -31,6 +34,7 @@
 
 #include <mutex>
 
+#include "convert.cuh"
 #include "decode_dest.cuh"
 #include "ptx.cuh"
 #include "tc_gemm.cuh"
@@ -46,6 +50,10 @@ constexpr int kThreads = 192;
 constexpr int kStageLd = 36;
 constexpr size_t kStageBytes = 4 * 32 * kStageLd * sizeof(float);
 constexpr uint64_t kWaitNs = 2000000000ull;
+// K blocks (64 elements) per accumulator chunk of the f16x3 mode.  Its main products h0*h0' carry
+// 22 significant bits, and the tensor cores' truncating accumulation drops low bits of them
+// (biased toward zero where the terms share a sign), so its chunks are shorter than bf16x6's.
+constexpr int kChunkF16x3 = 1;
 
 struct Params {
   TcInst one;                 // the instance of a single product
@@ -118,11 +126,13 @@ template <int P, int BN, int STAGES>
 constexpr bool kTwoPerSm = P == 1 && BN == 128 && STAGES == 2;
 
 // P: stored panels per operand (1 plain, 2 split [hi | lo], 3 bf16x6 [b0 | b1 | b2]).
-template <int KIND, int P, int BN, int STAGES, bool GROUPED>
+// SC: f16x3 (P = 2, scaled fp16 panels [h0 | h1], main and cross-term accumulators).
+template <int KIND, int P, int BN, int STAGES, bool GROUPED, bool SC>
 __global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ Tables<float> t, const Params p) {
   static_assert(P >= 1 && P <= 3 && (P < 3 || KIND == 0), "three panels are bf16 only");
+  static_assert(!SC || (P == 2 && KIND == 0), "f16x3 keeps two fp16 panels");
   constexpr uint32_t A_BYTES = BM * kRowBytes, B_BYTES = BN * kRowBytes;
   constexpr uint32_t STAGE_BYTES = P * (A_BYTES + B_BYTES);
   constexpr int KSTEPS = kRowBytes / 32;  // MMA K steps per stage (32 bytes of K in A rows)
@@ -134,12 +144,13 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
   // right operand is stored transposed (T^T, rows n) and loaded like S.
   constexpr bool BMN = KIND == 0;
   // The tensor cores accumulate in fp32 with truncation, whose error grows with the number of
-  // accumulations into one sum.  bf16x6 tiles therefore accumulate chunks of KCH K blocks
-  // (256 elements of K) in TMEM, each in two accumulators (main term, cross terms), and the
-  // epilogue adds the chunks in fp32 registers with round-to-nearest.  Other modes accumulate
-  // a whole tile in one accumulator.
-  constexpr int KCH = P == 3 ? 4 : (1 << 30);
-  constexpr int ACC_COLS = P == 3 ? 2 * BN : BN;  // TMEM columns of one accumulator buffer
+  // accumulations into one sum.  bf16x6 and f16x3 tiles therefore accumulate chunks of KCH K
+  // blocks (256 elements of K) in TMEM, each in two accumulators (main term, cross terms), and
+  // the epilogue adds the chunks in fp32 registers with round-to-nearest.  Other modes
+  // accumulate a whole tile in one accumulator.
+  constexpr bool TWO_ACC = P == 3 || SC;
+  constexpr int KCH = P == 3 ? 4 : (SC ? kChunkF16x3 : (1 << 30));
+  constexpr int ACC_COLS = TWO_ACC ? 2 * BN : BN;  // TMEM columns of one accumulator buffer
   static_assert(2 * ACC_COLS <= 512, "two accumulator buffers fit TMEM");
 
   extern __shared__ uint8_t smem_raw[];
@@ -287,6 +298,13 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
               ptx::mma<KIND>(d_small, ad[0], bd[1], p.idesc, 1u);
               ptx::mma<KIND>(d_small, ad[1], bd[0], p.idesc, 1u);
               ptx::mma<KIND>(d_tmem, ad[0], bd[0], p.idesc, acc);
+            } else if constexpr (SC) {
+              // h0*h1' + h1*h0' (at most 2^-10 of the leading term) into the cross-term
+              // accumulator, h0*h0' alone into the main one
+              const uint32_t d_small = d_tmem + (uint32_t)BN;
+              ptx::mma<KIND>(d_small, ad[0], bd[1], p.idesc, acc);
+              ptx::mma<KIND>(d_small, ad[1], bd[0], p.idesc, 1u);
+              ptx::mma<KIND>(d_tmem, ad[0], bd[0], p.idesc, acc);
             } else if constexpr (P == 2) {
               ptx::mma<KIND>(d_tmem, ad[0], bd[1], p.idesc, acc);
               ptx::mma<KIND>(d_tmem, ad[1], bd[0], p.idesc, 1u);
@@ -391,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
         __syncwarp();  // the block is read before the next one overwrites it
       };
       int ok = 1;
-      if constexpr (P == 3) {
+      if constexpr (TWO_ACC) {
         // chunks of the tile's K: sum main and cross-term accumulators in registers (fp32,
         // round to nearest), releasing each accumulator buffer as soon as it is read
         const int nch = (d.nk + KCH - 1) / KCH;
@@ -409,8 +427,10 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
           for (int c0 = 0; c0 < BN; c0 += 32) {
             float x[32];
             ptx::tmem_ld32(tb + (uint32_t)(BN + c0), x);  // cross terms
+            // f16x3: the low pieces were stored times 2^11 (exact scaling back)
+            constexpr float cs = SC ? 1.f / kF16LoScale : 1.f;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) sum[c0 + i] += x[i];
+            for (int i = 0; i < 32; ++i) sum[c0 + i] += SC ? x[i] * cs : x[i];
             ptx::tmem_ld32(tb + (uint32_t)c0, x);         // main term
 #pragma unroll
             for (int i = 0; i < 32; ++i) sum[c0 + i] += x[i];
@@ -427,11 +447,25 @@ __global__ void __launch_bounds__(kThreads, kTwoPerSm<P, BN, STAGES> ? 2 : 1)
           if (lane == 0) raise_abort(abort, p.status);
           break;
         }
+        float rs = 1.f;
+        if constexpr (SC) rs = d.rinv[(int64_t)tm * BM + quarter * 32 + lane];  // this lane's row
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 32) {
           float v[32];
+          if constexpr (SC) {
+            const float4* cs = reinterpret_cast<const float4*>(d.cinv + (int64_t)tn * BN + c0);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = sum[c0 + i];
+            for (int q = 0; q < 8; ++q) {
+              const float4 c = cs[q];  // powers of two: the products below are exact
+              v[4 * q] = sum[c0 + 4 * q] * (rs * c.x);
+              v[4 * q + 1] = sum[c0 + 4 * q + 1] * (rs * c.y);
+              v[4 * q + 2] = sum[c0 + 4 * q + 2] * (rs * c.z);
+              v[4 * q + 3] = sum[c0 + 4 * q + 3] * (rs * c.w);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = sum[c0 + i];
+          }
           out_block(v, c0);
         }
       } else {
@@ -499,7 +533,7 @@ bool make_map(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int es
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KIND, int P, int BN, int STAGES, bool GROUPED>
+template <int KIND, int P, int BN, int STAGES, bool GROUPED, bool SC = false>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<float>& t, const Params& p,
                    cudaStream_t st) {
   constexpr size_t smem =
@@ -509,7 +543,7 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Tables<fl
   // a CTA of any other configuration takes more than half of the SM's shared memory, so it never
   // shares an SM (and its TMEM) with another CTA of this kernel
   static_assert(kTwoPerSm<P, BN, STAGES> || 2 * (smem + 1024) > 233472, "one CTA per SM");
-  auto kern = tc_gemm_kernel<KIND, P, BN, STAGES, GROUPED>;
+  auto kern = tc_gemm_kernel<KIND, P, BN, STAGES, GROUPED, SC>;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   // Once per device (never inside a later stream capture): allow the large shared memory.
@@ -544,6 +578,12 @@ cudaError_t dispatch(int leaf, int bn, int ctas, const CUtensorMap& ma, const CU
     if (ctas != 1 || bn != 128) return cudaErrorInvalidValue;
     return launch<0, 3, 128, 2, GROUPED>(ma, mb, t, p, st);
   }
+  if (leaf == RBC_LEAF_F16X3) {
+    // two 16 KB panels of A and of B per stage: three stages of 64 KB at 128-wide tiles (two
+    // accumulator buffers of main and cross terms fill TMEM)
+    if (ctas != 1 || bn != 128) return cudaErrorInvalidValue;
+    return launch<0, 2, 128, 3, GROUPED, true>(ma, mb, t, p, st);
+  }
   if (ctas != 1) {
     if (ctas != 2 || split || bn != 128) return cudaErrorInvalidValue;
     return tf32 ? launch<1, 1, 128, 2, GROUPED>(ma, mb, t, p, st) : launch<0, 1, 128, 2, GROUPED>(ma, mb, t, p, st);
@@ -567,7 +607,7 @@ cudaError_t dispatch(int leaf, int bn, int ctas, const CUtensorMap& ma, const CU
 
 uint32_t leaf_idesc(int leaf, int bn) {
   const bool tf32 = leaf == RBC_LEAF_TF32 || leaf == RBC_LEAF_3XTF32;
-  const uint32_t fmt = tf32 ? 2u : (leaf == RBC_LEAF_F16 ? 0u : 1u);
+  const uint32_t fmt = tf32 ? 2u : ((leaf == RBC_LEAF_F16 || leaf == RBC_LEAF_F16X3) ? 0u : 1u);
   return ptx::idesc(fmt, fmt, BM, bn, tf32 ? 0u : 1u);
 }
 
@@ -577,6 +617,7 @@ int64_t tc_pad(int64_t m) { return (m + 127) / 128 * 128; }
 
 int tc_default_bn(int leaf, int64_t mp) {
   if (leaf == RBC_LEAF_BF16X6) return 128;  // a 256-wide stage of three panel pairs does not fit twice
+  if (leaf == RBC_LEAF_F16X3) return 128;   // two accumulator buffers of main and cross terms: 4 x 128 columns
   return mp % 256 == 0 ? 256 : 128;
 }
 
@@ -591,9 +632,10 @@ bool tc_prepare_instance(const TcGemmArgs& a, int bn, int group_m, int64_t tile_
   const bool tf32 = a.leaf == RBC_LEAF_TF32 || a.leaf == RBC_LEAF_3XTF32;
   const int es = tf32 ? 4 : 2;
   const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                      : (a.leaf == RBC_LEAF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                      : ((a.leaf == RBC_LEAF_F16 || a.leaf == RBC_LEAF_F16X3) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   if (a.mp % 128 || a.mp % bn) return false;
+  if (a.leaf == RBC_LEAF_F16X3 && (!a.rinv || !a.cinv)) return false;
   const int64_t rows = a.leaves * a.mp;
   if (rows > INT32_MAX || a.K > INT32_MAX) return false;
   CUtensorMap* m = static_cast<CUtensorMap*>(maps2);
@@ -619,6 +661,8 @@ bool tc_prepare_instance(const TcGemmArgs& a, int bn, int group_m, int64_t tile_
   x.M = static_cast<float*>(a.M);
   x.ldm = a.mp;
   x.strideM = a.strideM;
+  x.rinv = a.rinv;
+  x.cinv = a.cinv;
   *d = x;
   return true;
 }
@@ -630,7 +674,8 @@ cudaError_t launch_tc_gemm(const Tables<float>& t, const TcGemmArgs& a, cudaStre
   // tiles have at most four K blocks, and the second CTA overlaps one CTA's epilogue with the
   // other's loads (bf16 Laderman leaves of 243 -> 256: 1.05 -> 0.92 ms per launch; at 512 the
   // 256-wide single CTA per SM stays faster, 0.76 against 0.93 ms).
-  const bool pair = !(a.leaf == RBC_LEAF_3XBF16 || a.leaf == RBC_LEAF_3XTF32 || a.leaf == RBC_LEAF_BF16X6) &&
+  const bool pair = !(a.leaf == RBC_LEAF_3XBF16 || a.leaf == RBC_LEAF_3XTF32 || a.leaf == RBC_LEAF_BF16X6 ||
+                      a.leaf == RBC_LEAF_F16X3) &&
                     a.mp <= 256;
   const int bn = pair ? 128 : tc_default_bn(a.leaf, a.mp);
   CUtensorMap maps[2];

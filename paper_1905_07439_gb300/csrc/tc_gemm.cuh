@@ -24,6 +24,8 @@ struct TcGemmArgs {
   int leaf;        // rbc_leaf_dtype
   int* status;     // device status word (RBC_ETIMEOUT on an expired wait)
   int stall;       // test hook: issue no operand copies (the bounded waits then expire)
+  const float* rinv;  // f16x3: inverse scales of the rows of S and the columns of T (mp each,
+  const float* cinv;  // powers of two), applied to every product entry; null otherwise
 };
 
 // One instance of a (possibly grouped) leaf-product launch, as the kernel reads it.
@@ -37,6 +39,8 @@ struct TcInst {
   int64_t ldc;
   float* M;
   int64_t ldm, strideM;
+  const float* rinv;  // f16x3: inverse row / column scales (see TcGemmArgs)
+  const float* cinv;
 };
 
 // A grouped launch: the leaf products of many instances (same leaf mode and tile width) in

@@ -16,12 +16,13 @@ from .build import LIB
 # enums (include/rbc.h)
 RBC_OK, RBC_EINVAL, RBC_ENOMEM, RBC_ECUDA, RBC_ETIMEOUT, RBC_EBUSY, RBC_EKAPPA, RBC_EUNSUPPORTED = range(8)
 IO_F64, IO_F32 = 0, 1
-LEAF_F64, LEAF_F32, LEAF_TF32, LEAF_BF16, LEAF_F16, LEAF_3XBF16, LEAF_3XTF32, LEAF_BF16X6 = range(8)
+LEAF_F64, LEAF_F32, LEAF_TF32, LEAF_BF16, LEAF_F16, LEAF_3XBF16, LEAF_3XTF32, LEAF_BF16X6, LEAF_F16X3 = range(9)
 RAND_FULL, RAND_SIGN, RAND_PERM, RAND_NONE = range(4)
 DRAW_PER_NODE, DRAW_PER_LEVEL = 0, 1
 ERR_EACH, ERR_AVERAGE = 0, 1
 LEAF_NAMES = {"f64": LEAF_F64, "f32": LEAF_F32, "tf32": LEAF_TF32, "bf16": LEAF_BF16,
-              "f16": LEAF_F16, "3xbf16": LEAF_3XBF16, "3xtf32": LEAF_3XTF32, "bf16x6": LEAF_BF16X6}
+              "f16": LEAF_F16, "3xbf16": LEAF_3XBF16, "3xtf32": LEAF_3XTF32, "bf16x6": LEAF_BF16X6,
+              "f16x3": LEAF_F16X3}
 
 
 class rbc_plan_desc(C.Structure):

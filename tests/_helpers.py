@@ -6,7 +6,7 @@ from rbc_inputs import formula_by_name, laderman, perturbed, strassen
 
 # Normwise gate ||C - C_oracle||_F / (||A||_F ||B||_F) <= t * g^L / sqrt(N) per leaf mode
 # (t at L = 0; g = 2 per level for n0 = 2 formulas, 3 for n0 = 3).
-GATE_T = {"f32": 2e-5, "bf16x6": 2e-5, "3xtf32": 2e-5, "3xbf16": 4e-5, "tf32": 1e-3, "f16": 1e-3, "bf16": 8e-3}
+GATE_T = {"f32": 2e-5, "bf16x6": 2e-5, "f16x3": 2e-5, "3xtf32": 2e-5, "3xbf16": 4e-5, "tf32": 1e-3, "f16": 1e-3, "bf16": 8e-3}
 
 
 def formula(name, seed=0):

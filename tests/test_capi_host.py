@@ -130,13 +130,16 @@ def test_workspace_sizes(rbc):
     ws5 = p5.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16, decode=1)
     body5 = 2 * 4 * 7 * 4096**2 + 2 * 2 * 16807 * 256**2
     assert body5 <= ws5 <= body5 + 4096
-    assert body <= ws4 <= body + 4096
     # split leaves store two bf16 panels per operand, bf16x6 three: the leaf operand bytes
-    # grow by one and two panels
+    # grow by one and two panels; f16x3 stores two fp16 panels and six scale vectors of mp = 512
+    # entries (row and column maxima, scales and their inverses)
     panel = 2 * 2 * 2401 * 512**2
     ws4_3x = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_3XBF16, decode=1)
     ws4_6x = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_BF16X6, decode=1)
+    ws4_h3 = p4.workspace_size(8192, rbc.IO_F32, rbc.LEAF_F16X3, decode=1)
     assert ws4_3x - ws4 == panel and ws4_6x - ws4 == 2 * panel
+    assert ws4_h3 - ws4 == panel + 6 * 512 * 4
+    assert p4.workspace_size(8192, rbc.IO_F64, rbc.LEAF_F16X3) == 0   # fp32 I/O only
 
 
 def test_laderman_encode_passes_cover_two_levels(rbc):
@@ -214,6 +217,8 @@ def test_group_configuration_validation(rbc):
         (ragged, rbc.LEAF_TF32, [(128, 8, 1), (128, 0, 2)], [(256, 0, 1), (256, 8, 2)]),
         # three panels per operand: only 128-wide tiles fit two stages
         (aligned, rbc.LEAF_BF16X6, [(128, 0, 1), (128, 8, 1)], [(256, 0, 1), (128, 0, 2)]),
+        # main and cross-term accumulator buffers fill TMEM at 128-wide tiles
+        (aligned, rbc.LEAF_F16X3, [(128, 0, 1), (128, 4, 1)], [(256, 0, 1), (128, 0, 2)]),
     ]
     for specs, leaf, good, bad in cases:
         h, plans = _fake_group(rbc, specs, leaf)

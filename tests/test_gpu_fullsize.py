@@ -118,7 +118,7 @@ def test_deep_plans_sampled_parity(rbc, name, n, L):
     assert ent <= egate("bf16x6", n0, L), (name, n, L, ent)
 
 
-@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f32"])
+@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f16x3", "f32"])
 def test_precision_sweep_sampled_parity(rbc, leaf):
     n, L = 16384, 2
     g = torch.Generator(device="cpu")
@@ -130,7 +130,8 @@ def test_precision_sweep_sampled_parity(rbc, leaf):
     assert ent <= egate(leaf, n0, L), (leaf, ent)
 
 
-@pytest.mark.parametrize("name,L,leaf", [("strassen", 2, "bf16x6"), ("laderman", 2, "bf16x6"),
+@pytest.mark.parametrize("name,L,leaf", [("strassen", 2, "bf16x6"), ("laderman", 2, "bf16x6"), ("strassen", 2, "f16x3"),
+                                         ("laderman", 2, "f16x3"),
                                          ("strassen", 2, "3xbf16")])
 def test_hard_inputs_sampled_parity(rbc, name, L, leaf):
     """The badly scaled case: Uniform[0,1] with rows of A and columns of B scaled by

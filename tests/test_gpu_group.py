@@ -41,7 +41,7 @@ def _batch(rbc, specs, seed):
     return plans, As, Bs, Cs
 
 
-@pytest.mark.parametrize("leaf", ["bf16", "3xbf16", "tf32", "bf16x6"])
+@pytest.mark.parametrize("leaf", ["bf16", "3xbf16", "tf32", "bf16x6", "f16x3"])
 @pytest.mark.parametrize("specs", [ALIGNED, RAGGED], ids=["aligned", "ragged"])
 def test_group_equals_individual_products(rbc, specs, leaf):
     plans, As, Bs, Cs = _batch(rbc, specs, seed=3)
@@ -95,7 +95,7 @@ def test_graph_replay_and_tuning_keep_results(rbc):
 CONFIGS = [(128, 0, 1), (128, 1, 2), (128, 8, 2), (128, 16, 1), (256, 2, 1)]
 
 
-@pytest.mark.parametrize("leaf", ["bf16", "tf32", "bf16x6"])
+@pytest.mark.parametrize("leaf", ["bf16", "tf32", "bf16x6", "f16x3"])
 @pytest.mark.parametrize("specs", [ALIGNED, RAGGED], ids=["aligned", "ragged"])
 def test_every_configuration_gives_the_same_products(rbc, specs, leaf):
     """Tile width, tile order and CTAs per SM (rbc_group_configure) change the speed only:
@@ -107,9 +107,9 @@ def test_every_configuration_gives_the_same_products(rbc, specs, leaf):
     side = torch.cuda.Stream()
     first = {}
     for bn, group, ctas in CONFIGS:
-        if (bn == 256 and specs is RAGGED) or (leaf == "bf16x6" and (bn == 256 or ctas == 2)):
-            # 256-wide tiles need padded leaves divisible by 256; bf16x6 takes 128-wide tiles,
-            # one CTA per SM
+        if (bn == 256 and specs is RAGGED) or (leaf in ("bf16x6", "f16x3") and (bn == 256 or ctas == 2)):
+            # 256-wide tiles need padded leaves divisible by 256; bf16x6 and f16x3 take
+            # 128-wide tiles, one CTA per SM
             with pytest.raises(rbc.RbcError) as e:
                 grp.configure(bn, group, ctas)
             assert e.value.status == 1

@@ -162,7 +162,7 @@ TC_CASES = [
 ]
 
 
-@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6"])
+@pytest.mark.parametrize("leaf", ["tf32", "bf16", "f16", "3xbf16", "3xtf32", "bf16x6", "f16x3"])
 @pytest.mark.parametrize("decode", [1, 2])
 @pytest.mark.parametrize("name,L,N", TC_CASES)
 def test_tensor_core_leaves_match_oracle(rbc, name, L, N, decode, leaf):
@@ -234,10 +234,53 @@ def test_bf16x6_is_as_accurate_as_fp32_leaves(rbc, name, L, N, dist):
         assert e6 < e3 / 4, (e6, e3)
 
 
+F16X3_CASES = [
+    # formula, L, N, input class: zero-mean, badly scaled rows and columns (1e-3 .. 1e3), and
+    # whole matrices far outside the fp16 range (2^-70 / 2^-40, 2^60 / 2^30), ragged leaves,
+    # the classical product, both decodes
+    ("strassen", 2, 4 * 200, "normal", 2),
+    ("strassen", 1, 2 * 300, "hard", 2),
+    ("strassen", 2, 4 * 128, "tiny", 1),
+    ("strassen", 2, 4 * 128, "huge", 2),
+    ("laderman", 2, 9 * 37, "normal", 2),
+    ("noisy-strassen", 3, 8 * 50, "hard", 2),
+    ("strassen", 0, 300, "huge", 0),
+]
+
+
+@pytest.mark.parametrize("name,L,N,dist,decode", F16X3_CASES)
+def test_f16x3_is_as_accurate_as_fp32_leaves(rbc, name, L, N, dist, decode):
+    """The f16x3 mode scales each leaf row of S and column of T by a power of two (from the row
+    and column maxima of A and B and the formula's growth bound), stores two fp16 pieces (22
+    significant bits) and drops only h1*h1' (2^-22 of the leading product): its distance to the
+    fp64 oracle (same draws) stays within twice the fp32 CUDA-core leaves' on the same inputs, and
+    within the fp32 gates, whatever the inputs' magnitude."""
+    U, V, W = formula(name, seed=4)
+    base = "normal" if dist in ("tiny", "huge") else dist
+    A, B = matrix_pair(base, N, seed=50 + L)
+    if dist == "tiny":
+        A, B = A * 2.0**-70, B * 2.0**-40
+    elif dist == "huge":
+        A, B = A * 2.0**60, B * 2.0**30
+    A = A.astype(np.float32).astype(np.float64)
+    B = B.astype(np.float32).astype(np.float64)
+    plan = rbc.Plan(U, V, W, levels=L, seed=909)
+    ref = o.rbc(A, B, oracle_plan(U, V, W, L, 909))
+    e32 = rel(gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_F32, decode), ref)
+    C3 = gpu_rbc(rbc, plan, A, B, torch.float32, rbc.LEAF_F16X3, decode)
+    e3 = rel(C3, ref)
+    assert e3 <= 2.0 * e32, (e3, e32)
+    n0 = U.shape[0]
+    assert entrywise(C3, ref, A, B, n0, L, mixed=dist == "hard") <= egate("f16x3", n0, L)
+    if dist != "hard":
+        assert normwise(C3, ref, A, B) <= gate("f16x3", n0, L, N)
+
+
 # Rounding of each leaf mode in the oracle's emulated-precision recursion (Section 2.2 model,
 # every operation rounded): fp32 for the fp32-accurate modes, the leaf storage format for the
 # others (the GPU accumulates in fp32, so it is never worse than rounding everything).
-EMULATED = {"f32": o.round_fp32, "bf16x6": o.round_fp32, "3xtf32": o.round_tf32, "tf32": o.round_tf32,
+EMULATED = {"f32": o.round_fp32, "bf16x6": o.round_fp32, "f16x3": o.round_fp32, "3xtf32": o.round_tf32,
+            "tf32": o.round_tf32,
             "3xbf16": o.round_bf16, "bf16": o.round_bf16, "f16": o.round_fp16}
 
 
@@ -262,7 +305,7 @@ def test_error_within_emulated_precision(rbc, name, L, N, leaf):
 
 @pytest.mark.parametrize("L,m,scope", [(2, 31, o.DRAW_PER_NODE), (2, 32, o.DRAW_PER_NODE), (2, 33, o.DRAW_PER_LEVEL),
                                        (2, 130, o.DRAW_PER_NODE), (3, 33, o.DRAW_PER_NODE), (3, 36, o.DRAW_PER_LEVEL)])
-@pytest.mark.parametrize("leaf", ["f32", "bf16x6", "bf16"])
+@pytest.mark.parametrize("leaf", ["f32", "bf16x6", "bf16", "f16x3"])
 def test_laderman_two_level_encode(rbc, L, m, scope, leaf):
     """fp32 encodes of Laderman's formula run two levels per pass for leaves of at least 32 (the
     first level in shared memory, 128-position tiles): leaves across that threshold, ragged and
@@ -294,7 +337,7 @@ DEEP_N02 = [
 
 
 @pytest.mark.parametrize("name,L,m,scope", DEEP_N02)
-@pytest.mark.parametrize("leaf", ["f32", "bf16x6", "bf16", "tf32"])
+@pytest.mark.parametrize("leaf", ["f32", "bf16x6", "bf16", "tf32", "f16x3"])
 def test_n0_2_deep_encode(rbc, name, L, m, scope, leaf):
     """fp32 encodes of n0 = 2 formulas with R <= 8 run three- and four-level passes, the first one
     or two levels split over the CTAs (tf32 leaves keep two-level passes: their last pass
@@ -328,7 +371,8 @@ def test_workspace_status_word_clear_after_calls(rbc):
     assert st.value == 0
 
 
-@pytest.mark.parametrize("leaf,decode", [("bf16", 2), ("3xbf16", 2), ("bf16", 1), ("bf16x6", 2), ("bf16x6", 1)])
+@pytest.mark.parametrize("leaf,decode", [("bf16", 2), ("3xbf16", 2), ("bf16", 1), ("bf16x6", 2), ("bf16x6", 1),
+                                         ("f16x3", 2), ("f16x3", 1)])
 def test_expired_wait_reports_timeout_and_the_context_survives(rbc, leaf, decode):
     """Failure detection without a fault.  With the stall test hook the leaf kernel issues no
     operand copies, so its MMA warp's bounded wait (2 s) expires: the kernel records

@@ -30,7 +30,8 @@ MIX = [("strassen", 1, 512, "bf16"), ("laderman", 1, 3 * 128, "3xbf16"), ("noisy
        ("strassen", 1, 2048, "3xbf16"), ("noisy-strassen", 1, 2 * 300, "tf32"), ("laderman", 1, 3 * 200, "f16"),
        ("strassen", 2, 1536, "bf16"), ("strassen", 1, 256, "f32"), ("laderman", 2, 9 * 128, "3xbf16"),
        ("strassen", 2, 4 * 256, "bf16x6"), ("laderman", 1, 3 * 256, "bf16x6"), ("strassen", 1, 512, "bf16"),
-       ("strassen", 1, 512, "bf16"), ("noisy-strassen", 2, 4 * 128, "bf16x6"), ("strassen", 1, 2 * 384, "bf16x6")]
+       ("strassen", 1, 512, "bf16"), ("noisy-strassen", 2, 4 * 128, "bf16x6"), ("strassen", 1, 2 * 384, "bf16x6"),
+       ("strassen", 2, 4 * 128, "f16x3"), ("laderman", 1, 3 * 256, "f16x3")]
 
 
 def _requests(rbc, seed):
