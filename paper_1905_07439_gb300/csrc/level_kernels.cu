@@ -1542,32 +1542,68 @@ __global__ void __launch_bounds__(kThreadsX) copy_leaf_kernel(const PassArgs a) 
 namespace {
 
 // ------------------------------------------------------------------ f16x3 leaf operand scales
-// Largest |entry| of each class of rows (rows = 1: rows i == r mod m, over all columns) or of
-// columns (rows = 0: columns j == c mod m, over all rows) of an N x N fp32 matrix, as fp32 bit
-// patterns (non-negative floats order like their bits) gathered with atomicMax.  A CTA covers
-// 32 rows x 1024 columns: each warp reads whole 128-byte row segments.
+// Largest |entry| of each class of rows of A (rows i == r mod m, over all columns) and of each
+// class of columns of B (columns j == c mod m, over all rows), N x N fp32, as fp32 bit patterns
+// (non-negative floats order like their bits) gathered with atomicMax; blockIdx.z = 0 takes A,
+// 1 takes B.  A CTA covers 32 rows x 1024 columns; with V4 every thread reads 16-byte vectors
+// (8 per row of A, 32 rows of 4 columns of B), all loads of a thread issued before any max.
 constexpr int kAmaxRows = 32, kAmaxCols = 1024;
-__global__ void __launch_bounds__(256) fold_absmax_kernel(const float* __restrict__ X, int64_t N, int64_t ld,
-                                                          int64_t m, int rows, unsigned* __restrict__ amax) {
+template <bool V4>
+__global__ void __launch_bounds__(256) fold_absmax_kernel(const float* __restrict__ A, int64_t lda,
+                                                          const float* __restrict__ B, int64_t ldb, int64_t N,
+                                                          int64_t m, unsigned* __restrict__ amaxA,
+                                                          unsigned* __restrict__ amaxB) {
   const int64_t r0 = (int64_t)blockIdx.y * kAmaxRows, c0 = (int64_t)blockIdx.x * kAmaxCols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (rows) {
-    // warp w: rows r0 + w, r0 + w + 8, ...; lanes stride the columns
+  if (blockIdx.z == 0) {
+    // warp w: rows r0 + w + 8 i; lanes stride the columns
+#pragma unroll 1
     for (int rr = warp; rr < kAmaxRows; rr += 8) {
       const int64_t r = r0 + rr;
       if (r >= N) break;
+      const float* row = A + r * lda;
       float mx = 0.f;
-      for (int64_t c = c0 + lane; c < c0 + kAmaxCols && c < N; c += 32) mx = fmaxf(mx, fabsf(X[r * ld + c]));
+      if constexpr (V4) {
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int64_t c = c0 + 4 * (lane + 32 * q);
+          v[q] = c < N ? *reinterpret_cast<const float4*>(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+      } else {
+        for (int64_t c = c0 + lane; c < c0 + kAmaxCols && c < N; c += 32) mx = fmaxf(mx, fabsf(row[c]));
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0 && mx > 0.f) atomicMax(amax + r % m, __float_as_uint(mx));
+      if (lane == 0 && mx > 0.f) atomicMax(amaxA + r % m, __float_as_uint(mx));
     }
   } else {
-    // thread t: columns c0 + t, c0 + t + 256, ... over the CTA's rows
-    for (int64_t c = c0 + threadIdx.x; c < c0 + kAmaxCols && c < N; c += 256) {
-      float mx = 0.f;
-      for (int64_t r = r0; r < r0 + kAmaxRows && r < N; ++r) mx = fmaxf(mx, fabsf(X[r * ld + c]));
-      if (mx > 0.f) atomicMax(amax + c % m, __float_as_uint(mx));
+    if constexpr (V4) {
+      // thread t: columns c0 + 4t .. c0 + 4t + 3 over the CTA's 32 rows
+      const int64_t c = c0 + 4 * threadIdx.x;
+      if (c >= N) return;
+      float4 mx = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+      for (int rr = 0; rr < kAmaxRows; ++rr) {
+        const int64_t r = r0 + rr;
+        if (r >= N) break;
+        const float4 v = *reinterpret_cast<const float4*>(B + r * ldb + c);
+        mx = make_float4(fmaxf(mx.x, fabsf(v.x)), fmaxf(mx.y, fabsf(v.y)), fmaxf(mx.z, fabsf(v.z)),
+                         fmaxf(mx.w, fabsf(v.w)));
+      }
+      const float e[4] = {mx.x, mx.y, mx.z, mx.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (e[q] > 0.f) atomicMax(amaxB + (c + q) % m, __float_as_uint(e[q]));
+    } else {
+      for (int64_t c = c0 + threadIdx.x; c < c0 + kAmaxCols && c < N; c += 256) {
+        float mx = 0.f;
+        for (int64_t r = r0; r < r0 + kAmaxRows && r < N; ++r) mx = fmaxf(mx, fabsf(B[r * ldb + c]));
+        if (mx > 0.f) atomicMax(amaxB + c % m, __float_as_uint(mx));
+      }
     }
   }
 }
@@ -1591,12 +1627,16 @@ __global__ void leaf_scales_kernel(const unsigned* __restrict__ amax, int64_t m,
 
 }  // namespace
 
-cudaError_t launch_fold_absmax(const float* X, int64_t N, int64_t ld, int64_t m, int rows, unsigned* amax,
-                               cudaStream_t st) {
-  if (N <= 0 || m <= 0 || ld < N) return cudaErrorInvalidValue;
+cudaError_t launch_fold_absmax(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t N, int64_t m,
+                               unsigned* amaxA, unsigned* amaxB, cudaStream_t st) {
+  if (N <= 0 || m <= 0 || lda < N || ldb < N) return cudaErrorInvalidValue;
   const int64_t gy = (N + kAmaxRows - 1) / kAmaxRows, gx = (N + kAmaxCols - 1) / kAmaxCols;
   if (gy > 65535) return cudaErrorInvalidValue;
-  fold_absmax_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(X, N, ld, m, rows, amax);
+  // 16-byte vectors when every row starts aligned and N is a multiple of 4
+  const bool v4 = N % 4 == 0 && lda % 4 == 0 && ldb % 4 == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0;
+  const dim3 grid((unsigned)gx, (unsigned)gy, 2);
+  if (v4) fold_absmax_kernel<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, N, m, amaxA, amaxB);
+  else fold_absmax_kernel<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, N, m, amaxA, amaxB);
   return cudaGetLastError();
 }
 

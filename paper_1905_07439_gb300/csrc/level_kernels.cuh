@@ -81,11 +81,12 @@ cudaError_t launch_encode_pass(const Tables<float>& t, const PassArgs& a, int n0
 cudaError_t launch_decode_pass(const Tables<double>& t, const PassArgs& a, int n0, int g, cudaStream_t st);
 cudaError_t launch_decode_pass(const Tables<float>& t, const PassArgs& a, int n0, int g, cudaStream_t st);
 
-// Leaf operand scales of the f16x3 mode.  amax[0 .. m) (zeroed by the caller) receives, as
-// fp32 bit patterns, max |X[i][c]| over the rows i == r (mod m) of X (rows = 1) or max |X[r][j]|
-// over the columns j == c (mod m) (rows = 0); one launch.
-cudaError_t launch_fold_absmax(const float* X, int64_t N, int64_t ld, int64_t m, int rows, unsigned* amax,
-                               cudaStream_t st);
+// Leaf operand scales of the f16x3 mode.  amaxA[0 .. m) and amaxB[0 .. m) (zeroed by the caller)
+// receive, as fp32 bit patterns, max |A[i][c]| over the rows i == r (mod m) of A and max
+// |B[r][j]| over the columns j == c (mod m) of B (N x N fp32, leading dimensions lda, ldb); one
+// launch.
+cudaError_t launch_fold_absmax(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t N, int64_t m,
+                               unsigned* amaxA, unsigned* amaxB, cudaStream_t st);
 // scale[r] = 2^e with e the largest integer such that amax[r] * growth * 2^e <= 2^15 (1 for a
 // zero class or r >= m), inv[r] = 2^-e, for r < mp.
 cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, float growth, float* scale, float* inv,

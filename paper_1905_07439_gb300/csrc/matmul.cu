@@ -276,12 +276,13 @@ rbc_status leaf_scales(const rbc_plan_s* p, const Layout& lo, const void* A, int
   unsigned* amax = reinterpret_cast<unsigned*>(ws + lo.scales);
   float* f = reinterpret_cast<float*>(ws + lo.scales);
   cudaError_t e = cudaMemsetAsync(amax, 0, 2 * (size_t)lo.mp * sizeof(unsigned), st);
-  if (e == cudaSuccess) e = launch_fold_absmax(static_cast<const float*>(A), N, lda, lo.m, 1, amax, st);
-  if (e == cudaSuccess) e = launch_fold_absmax(static_cast<const float*>(B), N, ldb, lo.m, 0, amax + lo.mp, st);
+  if (e == cudaSuccess)
+    e = launch_fold_absmax(static_cast<const float*>(A), lda, static_cast<const float*>(B), ldb, N, lo.m, amax,
+                           amax + lo.mp, st);
   for (int tensor = 0; tensor < 2 && e == cudaSuccess; ++tensor)
     e = launch_leaf_scales(amax + tensor * lo.mp, lo.m, lo.mp, (float)std::min(leaf_growth(p, tensor), 1e30),
                            f + (2 + tensor) * lo.mp, f + (4 + tensor) * lo.mp, st);
-  g_launches += 4;
+  g_launches += 3;
   return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
 }
 
