@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--leaf", default=None,
-                    help="leaf mode; default for the sweep bf16x6: fp32 I/O with six-product bf16 tensor-core "
-                         "leaves, as accurate as fp32 arithmetic (3xbf16, bf16, ... are the precision sweep); "
+                    help="leaf mode; default for the sweep f16x3: fp32 I/O with three-product scaled fp16 "
+                         "tensor-core leaves, as accurate as fp32 arithmetic (bf16x6 the six-product bf16 "
+                         "alternative; 3xbf16, bf16, ... are the precision sweep); "
                          "default for the batch workload bf16")
     ap.add_argument("--cases", default="all", help="'all' or comma list of indices into the sweep")
     ap.add_argument("--no-e2e", action="store_true")
@@ -180,7 +181,7 @@ class ClockSampler:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the step's ten leaf launches,
 # summed over one ncu capture of the full sweep, keyed by (leaf mode, library version): a
 # capture describes the kernel it measured only, so another library version reports null.
-LEAF_TRAFFIC_STEP = {("bf16x6", 200): 46_604_675_328}
+LEAF_TRAFFIC_STEP = {("bf16x6", 200): 46_604_675_328, ("f16x3", 201): 34_500_083_968}
 # Stored panels per leaf operand and tensor-core products per leaf product of each leaf mode.
 LEAF_PANELS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 2, "3xtf32": 2, "bf16x6": 3, "f16x3": 2}
 LEAF_PRODUCTS = {"f32": 1, "tf32": 1, "bf16": 1, "f16": 1, "3xbf16": 3, "3xtf32": 3, "bf16x6": 6, "f16x3": 3}
@@ -972,7 +973,7 @@ def run_experiments(args):
         print(json.dumps(line))
 
 
-SERVE_LEAF = {"fp32": "bf16x6", "bf16-leaf": "bf16", "3xbf16-leaf": "3xbf16"}
+SERVE_LEAF = {"fp32": "f16x3", "bf16-leaf": "bf16", "3xbf16-leaf": "3xbf16"}
 
 
 def serve_specs(count: int, rate: float, seed: int = 5):
@@ -1102,7 +1103,7 @@ def serve_measure(specs, cap_gb, dev, local, baseline_sample=300):
 def serve_config(n_requests, rate, cap_gb):
     return (f"rbc-serve: {n_requests} requests, Poisson {rate:g}/s, n log-uniform [128,8192], "
             "strassen/laderman/noisy-strassen, L in {1,2,3} (clamped for small n), dtype in {fp32, bf16-leaf, "
-            f"3xbf16-leaf}} (fp32 served by bf16x6 leaves), workspace admission cap {cap_gb:g} GB, 16 streams")
+            f"3xbf16-leaf}} (fp32 served by f16x3 leaves), workspace admission cap {cap_gb:g} GB, 16 streams")
 
 
 def run_serve(args):
@@ -1117,7 +1118,7 @@ def run_serve(args):
     line = {
         "metric": METRIC, "value": m["requests_per_s"], "unit": "requests/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": m["span_ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 io; leaves per request (fp32 -> bf16x6, bf16, 3xbf16)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 io; leaves per request (fp32 -> f16x3, bf16, 3xbf16)",
         "data": "synthetic (seeded N(0,1); Poisson arrivals)",
         "config": {"workload": serve_config(len(specs), args.rate, args.cap_gb), "parallelism": "replicas x1"},
         "clocks": clk.summary(),
@@ -1193,7 +1194,7 @@ def main():
     elif args.workload == "precision":
         run_precision(args)
     else:
-        args.leaf = args.leaf or "bf16x6"
+        args.leaf = args.leaf or "f16x3"
         run_ours(args)
 
 

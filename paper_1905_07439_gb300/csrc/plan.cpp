@@ -309,6 +309,6 @@ const char* rbc_status_string(rbc_status s) {
 
 const char* rbc_last_error(void) { return g_last_error.c_str(); }
 
-int rbc_version(void) { return 200; }
+int rbc_version(void) { return 201; }
 
 }  // extern "C"

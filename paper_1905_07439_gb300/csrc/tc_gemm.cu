@@ -7,8 +7,9 @@
 //   warp 0     one thread issues TMA loads of the S tile (K-major) and the T tile (MN-major:
 //              T is stored row-major with n contiguous) with the 128-byte swizzle into a ring
 //              of shared-memory stages (mbarrier full/empty handshake);
-//   warp 1     allocates TMEM (two fp32 accumulators of 128 x BN; for bf16x6 two buffers of a
-//              main and a cross-term accumulator, drained every 256 elements of K) and one thread issues
+//   warp 1     allocates TMEM (two fp32 accumulators of 128 x BN; for bf16x6 and f16x3 two
+//              buffers of a main and a cross-term accumulator, drained every 256 (bf16x6) or
+//              64 (f16x3) elements of K) and one thread issues
 //              tcgen05.mma (M = 128, N = BN, K = 16 bf16/f16 or 8 tf32 per instruction),
 //              committing stage releases and accumulator-ready signals;
 //   warps 2-5  drain an accumulator with tcgen05.ld (one TMEM lane = one tile row per
