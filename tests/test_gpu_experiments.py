@@ -77,7 +77,7 @@ def test_batch_equals_single_calls(rbc, case, io):
         assert not torch.equal(Cs[0], Cs[1])  # different draws give different realizations
 
 
-@pytest.mark.parametrize("leaf", ["bf16", "3xbf16", "tf32"])
+@pytest.mark.parametrize("leaf", ["bf16", "3xbf16", "tf32", "f16x3"])
 def test_batch_equals_single_calls_tensor_core_leaves(rbc, leaf):
     U, V, W = formula("laderman")
     N, L, K = 9 * 40, 2, 5   # leaves of 40: two-level encode passes

@@ -42,6 +42,7 @@ def _static_call(rbc, plan, A, B, C, leaf):
 def test_static_scratch_matches_workspace_entry_point(rbc):
     cases = [("strassen", 2, 4 * 192, "bf16", torch.float32),
              ("laderman", 1, 3 * 120, "3xbf16", torch.float32),
+             ("strassen", 1, 2 * 300, "f16x3", torch.float32),   # leaf scales in the array too
              ("noisy-strassen", 2, 4 * 40, "f64", torch.float64)]
     g = torch.Generator(device="cuda")
     for i, (name, L, N, leaf_name, dt) in enumerate(cases):
