@@ -1608,17 +1608,18 @@ __global__ void __launch_bounds__(256) fold_absmax_kernel(const float* __restric
   }
 }
 
-__global__ void leaf_scales_kernel(const unsigned* __restrict__ amax, int64_t m, int64_t mp, float growth,
+__global__ void leaf_scales_kernel(const unsigned* __restrict__ amax, int64_t m, int64_t mp, double growth,
                                    float* __restrict__ scale, float* __restrict__ inv) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= mp) return;
   int e = 0;
   if (r < m) {
-    const float t = __uint_as_float(amax[r]) * growth;
-    if (t > 0.f && t <= 3.0e38f) {
+    // in fp64: the largest fp32 entries times the growth bound stay finite
+    const double t = (double)__uint_as_float(amax[r]) * growth;
+    if (t > 0.0) {
       int ex;
-      frexpf(t, &ex);  // t < 2^ex
-      e = min(max(15 - ex, -120), 120);
+      frexp(t, &ex);  // t < 2^ex
+      e = min(max(15 - ex, -126), 126);  // 2^e and 2^-e are normal fp32 numbers
     }
   }
   scale[r] = ldexpf(1.f, e);
@@ -1640,7 +1641,7 @@ cudaError_t launch_fold_absmax(const float* A, int64_t lda, const float* B, int6
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, float growth, float* scale, float* inv,
+cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, double growth, float* scale, float* inv,
                                cudaStream_t st) {
   if (mp <= 0 || m > mp) return cudaErrorInvalidValue;
   leaf_scales_kernel<<<(unsigned)((mp + 255) / 256), 256, 0, st>>>(amax, m, mp, growth, scale, inv);

@@ -87,9 +87,9 @@ cudaError_t launch_decode_pass(const Tables<float>& t, const PassArgs& a, int n0
 // launch.
 cudaError_t launch_fold_absmax(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t N, int64_t m,
                                unsigned* amaxA, unsigned* amaxB, cudaStream_t st);
-// scale[r] = 2^e with e the largest integer such that amax[r] * growth * 2^e <= 2^15 (1 for a
+// scale[r] = 2^e with e the largest integer such that amax[r] * growth * 2^e < 2^15 (1 for a
 // zero class or r >= m), inv[r] = 2^-e, for r < mp.
-cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, float growth, float* scale, float* inv,
+cudaError_t launch_leaf_scales(const unsigned* amax, int64_t m, int64_t mp, double growth, float* scale, float* inv,
                                cudaStream_t st);
 
 // Batched leaf products M_leaf = S_leaf * T_leaf on the CUDA cores (fp32 or fp64 FMA).

@@ -280,7 +280,7 @@ rbc_status leaf_scales(const rbc_plan_s* p, const Layout& lo, const void* A, int
     e = launch_fold_absmax(static_cast<const float*>(A), lda, static_cast<const float*>(B), ldb, N, lo.m, amax,
                            amax + lo.mp, st);
   for (int tensor = 0; tensor < 2 && e == cudaSuccess; ++tensor)
-    e = launch_leaf_scales(amax + tensor * lo.mp, lo.m, lo.mp, (float)std::min(leaf_growth(p, tensor), 1e30),
+    e = launch_leaf_scales(amax + tensor * lo.mp, lo.m, lo.mp, std::min(leaf_growth(p, tensor), 1e300),
                            f + (2 + tensor) * lo.mp, f + (4 + tensor) * lo.mp, st);
   g_launches += 3;
   return e == cudaSuccess ? RBC_OK : fail(RBC_ECUDA, cudaGetErrorString(e));
